@@ -1,0 +1,401 @@
+#!/usr/bin/env python
+"""Benchmark of the block ILU(k)-preconditioned BiCGSTAB hot path on one GB300.
+
+One step = everything that depends on the matrix values, on the resident
+inputs: backfill A -> A', block ILU factorization (Algorithm 4) with the
+diagonal factorization U = D U' (Eq. 5), then BiCGSTAB from x0 = 0 toward a
+true relative residual of 1e-8 with an iteration budget of --maxit (each
+iteration: two preconditioner applies (Eq. 6, Algorithm 7) and two block
+SpMVs).  The 128 x 128 x 64 workload (sigma = 2, accumulation 1e-3) does not
+reach 1e-8 with ILU(1)-BiCGSTAB (neither does the CPU oracle), so on it a
+step is the factorization plus exactly --maxit iterations; the line says
+whether the solve converged.  The 16 x 16 x 8 workload, which converges, is
+also timed to 1e-8 (``ms_to_tol_small``).  The symbolic phase (Algorithm 3)
+depends on the pattern only; it runs once at set-up and its host time is
+reported next to the step (``symbolic_ms``).
+
+Output: one JSON line (rank 0).  ``value`` is milliseconds per step (lower is
+better).  ``roofline`` reports the dominant kernel's algorithmic bytes per
+launch divided by its mean CUDA-event duration over the timed region, against
+the measured HBM copy bandwidth.  ``e2e`` repeats the step through the public
+API from pinned host buffers (A's values and the right-hand side copied in,
+x copied out, inside the timed region).  ``cpu_baseline`` is the CPU oracle
+timed on a bounded sample of the same workload.
+
+``--impl reference`` times the CPU oracle as the reference arm (no GPU use).
+"""
+from __future__ import annotations
+
+import argparse
+import ctypes as C
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "Block-ILU(k) BiCGSTAB ms to 1e-8 resid; trisolve/SpMV GB/s; FP32-prec vs FP64"
+WORKLOAD = "grid128x128x64_7pt_b3"
+FP64_PEAK_TFLOPS = 1.196  # measured FP64 FMA rate of this GB300 (FMA = 2 flops)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--k", type=int, default=1)
+    ap.add_argument("--tol", type=float, default=1e-8)
+    ap.add_argument("--maxit", type=int, default=100)
+    ap.add_argument("--chunk", type=int, default=0, help="trisolve rows per warp (0 = library default)")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    return ap.parse_args()
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def system(args):
+    from paper_1703_01325_gb300.reservoir import WORKLOADS, reservoir_system
+    cfg = dict(WORKLOADS[args.workload])
+    return reservoir_system(**cfg), cfg
+
+
+def algorithmic_bytes(n, b, nnz_a, nnz_l, nnz_u, v=8):
+    """Bytes a kernel must move at least once (values, indices, vectors)."""
+    bb = b * b
+    spmv = nnz_a * (v * bb + 4) + 4 * (n + 1) + 2 * n * b * v
+    lower = nnz_l * (v * bb + 4) + 4 * (n + 1) + 2 * n * b * v            # L, r in, y out
+    upper = nnz_u * (v * bb + 4) + n * v * bb + 4 * (n + 1) + 2 * n * b * v  # U', D^-1, y in, x out
+    return dict(spmv=spmv, lower_solve=lower, upper_solve=upper, apply=lower + upper)
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        import statistics
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, f[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_baseline(S, k, gpu_iters, sample_iters=4):
+    """The CPU oracle (single thread) on a bounded sample: the full symbolic
+    phase and factorization plus `sample_iters` BiCGSTAB iterations, scaled to
+    the iteration count of the measured solve."""
+    import oracle
+    t0 = time.perf_counter()
+    prp, pci, _ = oracle.symbolic(S.n, S.row_ptr, S.col_idx, k)
+    t1 = time.perf_counter()
+    A1 = oracle.backfill(S.n, S.b, S.row_ptr, S.col_idx, S.vals, prp, pci)
+    F, D = oracle.factor(S.n, S.b, prp, pci, A1)
+    t2 = time.perf_counter()
+    oracle.bicgstab(S.n, S.b, S.row_ptr, S.col_idx, S.vals, prp, pci, F, D, S.rhs, tol=1e-300,
+                    maxit=sample_iters)
+    t3 = time.perf_counter()
+    # bicgstab also pays one SpMV for r0 and one for the true residual
+    per_it = (t3 - t2) / sample_iters
+    factor_ms = (t2 - t1) * 1e3
+    value = factor_ms + per_it * 1e3 * max(gpu_iters, 1)
+    return {"value": round(value, 1), "unit": "ms", "cores": 1, "kind": "oracle",
+            "sample": (f"oracle factorization of the full matrix ({factor_ms:.0f} ms) + {sample_iters} "
+                       f"BiCGSTAB iterations ({per_it * 1e3:.0f} ms each), scaled to {gpu_iters} iterations; "
+                       f"symbolic {1e3 * (t1 - t0):.0f} ms not counted")}
+
+
+def run_reference(args):
+    """Reference arm: the CPU oracle as it stands, on the same workload."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+    S, cfg = system(args)
+    prp, pci, _ = oracle.symbolic(S.n, S.row_ptr, S.col_idx, args.k)
+    iters_ref = args.maxit  # the workload does not converge within the budget
+    sample_iters = 2
+
+    def step():
+        t1 = time.perf_counter()
+        A1 = oracle.backfill(S.n, S.b, S.row_ptr, S.col_idx, S.vals, prp, pci)
+        F, D = oracle.factor(S.n, S.b, prp, pci, A1)
+        t2 = time.perf_counter()
+        oracle.bicgstab(S.n, S.b, S.row_ptr, S.col_idx, S.vals, prp, pci, F, D, S.rhs, tol=1e-300,
+                        maxit=sample_iters)
+        t3 = time.perf_counter()
+        return (t2 - t1) * 1e3 + (t3 - t2) / sample_iters * 1e3 * iters_ref
+
+    for _ in range(args.warmup):
+        step()
+    vals = [step() for _ in range(args.steps)]
+    ms = sum(vals) / len(vals)
+    out = {
+        "impl": "reference", "metric": METRIC, "value": round(ms, 1), "unit": "ms", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 1), "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "k": args.k, "tol": args.tol, "maxit": args.maxit, **cfg,
+                   "step": "backfill + factor + BiCGSTAB iterations up to maxit"},
+        "cpu_baseline": {"value": round(ms, 1), "unit": "ms", "cores": 1, "kind": "oracle",
+                         "sample": f"per step: full factorization + {sample_iters} BiCGSTAB iterations, "
+                                   f"scaled to {iters_ref} iterations"},
+        "e2e": {"value": round(ms, 1), "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(out), flush=True)
+
+
+def ms_to_tol_small(B, dev, stream, reps=5):
+    """Factor + BiCGSTAB to 1e-8 on the 16 x 16 x 8, b = 3, ILU(1) workload,
+    which converges (launch/latency bound: it fits in L2)."""
+    import torch
+    from paper_1703_01325_gb300.reservoir import WORKLOADS, reservoir_system
+    S = reservoir_system(**WORKLOADS["grid16x16x8_7pt_b3"])
+    P = B.bilu_symbolic(S.n, S.row_ptr, S.col_idx, 1).upload()
+    rp, ci = torch.from_numpy(S.row_ptr).to(dev), torch.from_numpy(S.col_idx).to(dev)
+    vals, rhs = torch.from_numpy(S.vals.reshape(-1)).to(dev), torch.from_numpy(S.rhs).to(dev)
+    F = B.new_factors(P, S.b, dev)
+    fw = B.workspace(P.factor_workspace_bytes(S.b), dev)
+    sw = B.workspace(P.bicgstab_workspace_bytes(S.b), dev)
+    x = torch.zeros_like(rhs)
+    times, info = [], None
+    for r in range(reps + 2):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        B.bilu_factor(P, S.b, vals, F, fw)
+        x.zero_()
+        _, info = B.bicgstab_solve(P, (S.n, S.b, rp, ci, vals), F, rhs, x=x, tol=1e-8, maxit=1000, work=sw)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if r >= 2:
+            times.append(e0.elapsed_time(e1))
+    times.sort()
+    return {"workload": "grid16x16x8_7pt_b3", "k": 1, "ms": round(times[len(times) // 2], 3),
+            "iters": info.iters, "true_relres": info.true_relres, "status": info.status}
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import numpy as np
+    import torch
+
+    import paper_1703_01325_gb300.bilu as B
+    from paper_1703_01325_gb300 import _lib as L
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:  # independent replicas: the method does not shard (one system per GPU)
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device(f"cuda:{local}"))
+    dev = torch.device(f"cuda:{local}")
+    torch.cuda.set_device(dev)
+    lib = L.load()
+    if args.chunk:
+        B.bilu_set_trisolve_chunk(args.chunk)
+
+    S, cfg = system(args)
+    b = S.b
+    t0 = time.perf_counter()
+    P = B.bilu_symbolic(S.n, S.row_ptr, S.col_idx, args.k)
+    symbolic_ms = (time.perf_counter() - t0) * 1e3
+    P.upload()
+    info = P.info
+    rp = torch.from_numpy(S.row_ptr).to(dev)
+    ci = torch.from_numpy(S.col_idx).to(dev)
+    vals = torch.from_numpy(S.vals.reshape(-1)).to(dev)
+    rhs = torch.from_numpy(S.rhs).to(dev)
+    F = B.new_factors(P, b, dev)
+    fwork = B.workspace(P.factor_workspace_bytes(b), dev)
+    swork = B.workspace(P.bicgstab_workspace_bytes(b), dev)
+    x = torch.zeros_like(rhs)
+    A = (S.n, b, rp, ci, vals)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        B.bilu_factor(P, b, vals, F, fwork)
+        x.zero_()
+        _, si = B.bicgstab_solve(P, A, F, rhs, x=x, tol=args.tol, maxit=args.maxit, work=swork)
+        return si
+
+    for _ in range(args.warmup):
+        si = step()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    lib.bilu_profile_enable(1)
+    launches0 = lib.bilu_launch_count()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    iters = []
+    with ClockSampler(local) as clocks:
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(args.steps):
+            si = step()
+            iters.append((si.status, si.iters, si.true_relres))
+        e1.record(stream)
+        torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    launches = lib.bilu_launch_count() - launches0
+    prof = {}
+    for kid, name in enumerate(L.PROF_KERNELS):
+        nl, tm = C.c_int64(), C.c_double()
+        lib.bilu_profile_read(kid, C.byref(nl), C.byref(tm))
+        prof[name] = (nl.value, tm.value)
+    lib.bilu_profile_enable(0)
+    if dist:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+
+    ab = algorithmic_bytes(S.n, b, S.nnzb, info.nnz_l, info.nnz_u)
+    hbm, peak_src = peaks()
+    kern = {}
+    for name in ("spmv", "lower_solve", "upper_solve"):
+        nl, tm = prof[name]
+        if nl:
+            avg_ms = tm / nl
+            kern[name] = {"launches": nl, "avg_us": round(avg_ms * 1e3, 2),
+                          "gbs": round(ab[name] / (avg_ms * 1e-3) / 1e9, 1),
+                          "share": round(tm / (ms * args.steps), 3)}
+    top = max(kern, key=lambda k: kern[k]["share"]) if kern else None
+    roof = None
+    if top:
+        ach = kern[top]["gbs"]
+        roof = {"kernel": top, "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
+                "frac": round(ach / hbm, 3), "traffic": None, "peak_source": peak_src}
+
+    # end to end through the public API: pinned host A values and rhs in, x out
+    e2e = None
+    if not args.no_e2e:
+        h_vals = torch.from_numpy(S.vals.reshape(-1)).pin_memory()
+        h_rhs = torch.from_numpy(S.rhs).pin_memory()
+        h_x = torch.empty_like(h_rhs).pin_memory()
+        d_vals = torch.empty_like(vals)
+        d_rhs = torch.empty_like(rhs)
+
+        def e2e_step():
+            d_vals.copy_(h_vals, non_blocking=True)
+            d_rhs.copy_(h_rhs, non_blocking=True)
+            B.bilu_factor(P, b, d_vals, F, fwork)
+            x.zero_()
+            B.bicgstab_solve(P, (S.n, b, rp, ci, d_vals), F, d_rhs, x=x, tol=args.tol, maxit=args.maxit,
+                             work=swork)
+            h_x.copy_(x, non_blocking=True)
+
+        e2e_step()
+        torch.cuda.synchronize()
+        g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        g0.record(stream)
+        for _ in range(args.steps):
+            e2e_step()
+        g1.record(stream)
+        torch.cuda.synchronize()
+        e2e = {"value": round(g0.elapsed_time(g1) / args.steps, 3), "unit": "ms",
+               "h2d_bytes_per_step": int(h_vals.numel() * 8 + h_rhs.numel() * 8),
+               "d2h_bytes_per_step": int(h_x.numel() * 8)}
+
+    small = None
+    if rank == 0 and args.workload == WORKLOAD:
+        small = ms_to_tol_small(B, dev, stream)
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+    statuses = sorted({s for s, _, _ in iters})
+    gpu_iters = iters[-1][1]
+    cpu = None
+    if not args.no_cpu and world == 1:
+        cpu = cpu_baseline(S, args.k, gpu_iters)
+    factor_ms = prof["backfill"][1] + prof["factor"][1] + prof["scale_upper"][1] + prof["factor_init"][1]
+    out = {
+        "metric": METRIC, "value": round(ms, 3), "unit": "ms", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms, 3), "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "k": args.k, "tol": args.tol, "maxit": args.maxit, **cfg,
+                   "n": S.n, "nnzb": S.nnzb, "nnz_p": info.nnz_p, "levels_lower": info.nlev_l,
+                   "trisolve_chunk": B.bilu_get_trisolve_chunk(),
+                   "l2": "inputs larger than L2 (A values %.0f MB, factors %.0f MB)" % (
+                       S.nnzb * b * b * 8 / 1e6, P.factor_bytes(b) / 1e6),
+                   "step": "backfill + factor + BiCGSTAB from x0 = 0 toward tol, at most maxit iterations"},
+        "converged": statuses == [0], "solve_status": statuses, "iters": gpu_iters,
+        "true_relres": iters[-1][2],
+        "factor_ms": round(factor_ms / args.steps, 3), "symbolic_ms": round(symbolic_ms, 1),
+        "per_iteration_ms": round((ms - factor_ms / args.steps) / max(gpu_iters, 1), 4),
+        "ms_to_tol_small": small,
+        "kernels": kern, "roofline": roof, "e2e": e2e, "cpu_baseline": cpu,
+        "gpu_launches": int(launches), "clocks": clocks.summary(),
+        "fp64_alu": {"peak_tflops": FP64_PEAK_TFLOPS,
+                     "spmv_tflops": round(2 * S.nnzb * b * b / (kern["spmv"]["avg_us"] * 1e-6) / 1e12, 3)
+                     if "spmv" in kern else None},
+    }
+    print(json.dumps(out), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

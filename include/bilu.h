@@ -1,0 +1,265 @@
+/*
+ * bilu.h -- C ABI of the GB300 (sm_103a) block ILU(k) library.
+ *
+ * The method is the decoupled block-wise ILU(k) preconditioner of Yang, Liu,
+ * Zhong and Chen ("Decoupled Block-Wise ILU(k) Preconditioner on GPU"):
+ *   symbolic phase   -- level-of-fill pattern P' of the block graph (Section
+ *                       2.2, Algorithm 3, Eq. 1-2) and dependency levels
+ *                       (Section 2.4, Eq. 4);
+ *   factorization    -- A' = A backfilled onto P' (Algorithm 5), block ILU(0)
+ *                       on A' (Algorithm 4) and U = D U' (Eq. 5), D^{-1} stored;
+ *   preconditioning  -- L y = r, z = D^{-1} y, U' x = z (Eq. 6, Algorithm 7);
+ *   Krylov solve     -- BiCGSTAB (Section 1 names it among the Krylov methods)
+ *                       with the block SpMV y = A x.
+ *
+ * Conventions shared by every call:
+ *  - Block CSR (Section 2.1): row_ptr[n+1] and col_idx[nnzb] count blocks;
+ *    columns strictly increasing in every row; every row holds its diagonal
+ *    block.  Values hold nnzb blocks of b*b doubles, each block stored column
+ *    by column: element (r, c) of block t is vals[t*b*b + c*b + r].
+ *  - 1 <= b <= 8.  Block rows n < 2^31, pattern sizes < 2^31 blocks.
+ *  - "stream" is a cudaStream_t (NULL = legacy default stream).  Every device
+ *    call is stream ordered and returns once its work is enqueued unless the
+ *    call says it synchronises.
+ *  - The caller owns every device buffer passed in (vectors, values, factor
+ *    buffer, workspace).  The library allocates device memory only in
+ *    bilu_pattern_upload (set-up), never in factor, apply, SpMV or solve.
+ *  - Pointers prefixed d_ are device pointers on the current device; the
+ *    others are host pointers.  Input and output vectors must not alias.
+ *  - Every call returns a bilu_status code; no call aborts the process and no
+ *    kernel traps: device-side failures are written to an error word in the
+ *    workspace and reported by the next call that synchronises.
+ */
+#ifndef BILU_H
+#define BILU_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum bilu_status {
+  BILU_OK = 0,
+  BILU_ERR_ARG = 1,           /* invalid argument (null pointer, bad size, b out of range) */
+  BILU_ERR_PATTERN = 2,       /* unsorted/duplicate/out-of-range column or missing diagonal */
+  BILU_ERR_SINGULAR = 3,      /* zero or non-finite pivot block D_i; row in the info struct */
+  BILU_ERR_BREAKDOWN = 4,     /* BiCGSTAB breakdown: rho, (r_hat, v) or omega became 0 */
+  BILU_ERR_NOT_CONVERGED = 5, /* maxit iterations without reaching tol */
+  BILU_ERR_TIMEOUT = 6,       /* a bounded dependency wait inside a kernel ran out */
+  BILU_ERR_CUDA = 7,          /* a CUDA runtime call failed */
+  BILU_ERR_OOM = 8,           /* host or device allocation failed, or a size overflowed */
+  BILU_ERR_STATE = 9          /* pattern not uploaded, or workspace too small */
+};
+
+/* Static message for a status code; never NULL. */
+const char* bilu_status_string(int status);
+
+/* ------------------------------------------------------------------------ */
+/* Symbolic phase (host)                                                     */
+/* ------------------------------------------------------------------------ */
+
+typedef struct bilu_pattern bilu_pattern; /* opaque, library-owned */
+
+/*
+ * bilu_symbolic -- level-of-fill pattern P' of ILU(k) on the block graph.
+ * Section 2.3: every listed block of A is one point of the abstract point
+ * matrix, whatever its values.  Section 2.2, Algorithm 3 with Eq. 1 (level 0
+ * on A's pattern) and Eq. 2 (lev_ij = min(lev_ij, lev_ip + lev_pj + 1) over
+ * pivots p < i of level <= k); entries of level <= k are kept.  Also computes
+ * the dependency levels of Eq. 4 for the lower and the upper part.
+ *   n        number of block rows (>= 0)
+ *   row_ptr  host, n+1 entries, row_ptr[0] = 0
+ *   col_idx  host, row_ptr[n] entries
+ *   k        level of fill, >= 0 (k >= n means complete fill)
+ *   out      receives a new handle; free it with bilu_destroy_pattern
+ * Returns BILU_ERR_PATTERN for a malformed pattern, BILU_ERR_OOM if P' would
+ * exceed 2^31 - 1 blocks.  Host only; touches no GPU state.
+ */
+int bilu_symbolic(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, int32_t k,
+                  bilu_pattern** out);
+
+typedef struct {
+  int32_t n;       /* block rows */
+  int32_t k;       /* level of fill */
+  int64_t nnz_a;   /* blocks of A */
+  int64_t nnz_p;   /* blocks of P' (lower + diagonal + upper) */
+  int64_t nnz_l;   /* strictly lower blocks of P' */
+  int64_t nnz_u;   /* strictly upper blocks of P' */
+  int32_t nlev_l;  /* number of dependency levels of L (Eq. 4) */
+  int32_t nlev_u;  /* number of dependency levels of U' (reversed graph) */
+} bilu_pattern_info;
+
+/* Sizes of a pattern.  Host only. */
+int bilu_pattern_query(const bilu_pattern* p, bilu_pattern_info* info);
+
+/*
+ * bilu_pattern_export -- copy P' out to caller-allocated host arrays:
+ *   row_ptr[n+1], col_idx[nnz_p], lev[nnz_p] (level of fill of each entry),
+ *   lvl_lower[n], lvl_upper[n] (Eq. 4 levels, 0-based: the paper's l(i) - 1).
+ * Any output pointer may be NULL to skip it.  Host only.
+ */
+int bilu_pattern_export(const bilu_pattern* p, int32_t* row_ptr, int32_t* col_idx, int32_t* lev,
+                        int32_t* lvl_lower, int32_t* lvl_upper);
+
+/*
+ * bilu_pattern_upload -- copy the pattern's integer structure to the current
+ * device (set-up; allocates device memory owned by the handle, about
+ * 4*(2n + nnz_l + nnz_u + nnz_a) bytes).  Synchronises the stream.  Needed
+ * before bilu_factor, bilu_apply and bicgstab_solve.
+ */
+int bilu_pattern_upload(bilu_pattern* p, void* stream);
+
+/* Frees the handle and its device copy.  NULL is ignored. */
+void bilu_destroy_pattern(bilu_pattern* p);
+
+/* ------------------------------------------------------------------------ */
+/* Factor buffer layout                                                      */
+/* ------------------------------------------------------------------------ */
+/*
+ * The factors live in ONE caller-allocated device buffer of
+ * bilu_factor_bytes(p, b) bytes, b*b doubles per block, in three sections:
+ *   [0, nnz_l)                  L_ij, j < i, rows ascending, columns ascending
+ *                               (the strictly lower blocks of P');
+ *   [nnz_l, nnz_l + n)          D_i^{-1}, one block per row (Eq. 5);
+ *   [nnz_l + n, nnz_l + n + nnz_u)  U'_ij = D_i^{-1} U_ij, j > i, rows
+ *                               ascending, columns ascending.
+ * L and U' have identity diagonal blocks, which are not stored.
+ */
+size_t bilu_factor_bytes(const bilu_pattern* p, int32_t b);
+
+/* ------------------------------------------------------------------------ */
+/* Factorization (device)                                                    */
+/* ------------------------------------------------------------------------ */
+
+typedef struct {
+  int32_t status;       /* bilu_status of the factorization */
+  int32_t bad_row;      /* first block row whose pivot block was singular, else -1 */
+  double ms;            /* device time of the factorization (CUDA events) */
+} bilu_factor_info;
+
+/* Scratch bytes bilu_factor needs (per-row ready flags and counters). */
+size_t bilu_factor_workspace_bytes(const bilu_pattern* p, int32_t b);
+
+/*
+ * bilu_factor -- numeric factorization A ~ L D U' on the pattern P'.
+ * Algorithm 5 steps 3-5: A' = A with zero fill blocks (backfill), then
+ * Algorithm 4 in place, rows ascending, pivots p ascending:
+ *   A_ip <- A_ip D_p^{-1};  A_ij <- A_ij - A_ip U_pj  for (i,j),(p,j) in P';
+ * then D_i^{-1} (Gauss-Jordan with partial pivoting inside the b x b block)
+ * and U'_ij = D_i^{-1} U_ij (Eq. 5).
+ *   d_a_vals   device, nnz_a*b*b doubles: A's values on the pattern given to
+ *              bilu_symbolic
+ *   d_factors  device, bilu_factor_bytes(p, b) bytes, written (layout above)
+ *   d_work     device scratch of at least bilu_factor_workspace_bytes bytes;
+ *              contents on entry are ignored
+ *   info       may be NULL
+ * Synchronises the stream to read the device error word.  Returns
+ * BILU_ERR_SINGULAR (info->bad_row set) for a zero or non-finite pivot block.
+ */
+int bilu_factor(const bilu_pattern* p, int32_t b, const double* d_a_vals, double* d_factors,
+                void* d_work, size_t work_bytes, void* stream, bilu_factor_info* info);
+
+/* ------------------------------------------------------------------------ */
+/* Preconditioner apply (device)                                             */
+/* ------------------------------------------------------------------------ */
+
+/* Scratch bytes bilu_apply needs (the intermediate y = L^{-1} r and counters). */
+size_t bilu_apply_workspace_bytes(const bilu_pattern* p, int32_t b);
+
+/*
+ * bilu_apply -- x = M^{-1} r with M = L D U' (Eq. 6, Algorithm 7):
+ *   L y = r (rows ascending), z = D^{-1} y, U' x = z (rows descending).
+ * The D^{-1} product is fused into the U' solve (row i forms D_i^{-1} y_i
+ * before subtracting U'_ij x_j).  Both triangular solves run as single
+ * sync-free kernels: each row waits, with a bounded spin, for the rows it
+ * depends on.
+ *   d_factors  device, output of bilu_factor with the same b
+ *   d_r, d_x   device, n*b doubles each; must not alias
+ *   d_work     device scratch of at least bilu_apply_workspace_bytes bytes
+ * Asynchronous: a dependency wait that times out is recorded in the workspace
+ * error word (read it with bilu_workspace_status).
+ */
+int bilu_apply(const bilu_pattern* p, int32_t b, const double* d_factors, const double* d_r,
+               double* d_x, void* d_work, size_t work_bytes, void* stream);
+
+/*
+ * bilu_workspace_status -- synchronises the stream and returns the status the
+ * most recent bilu_apply on this workspace recorded in its device error word
+ * (BILU_OK or BILU_ERR_TIMEOUT).  Every bilu_apply clears the word first.
+ */
+int bilu_workspace_status(const void* d_work, void* stream);
+
+/* ------------------------------------------------------------------------ */
+/* Block SpMV (device)                                                       */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * bsr_spmv -- y = A x for a block CSR matrix (the SpMV Section 2.4 relies
+ * on; each block row summed over its blocks in column order).
+ *   n, b                 block rows and block size
+ *   d_row_ptr, d_col_idx device pattern (as for bilu_symbolic; the diagonal is
+ *                        not required here)
+ *   d_vals               device, nnzb*b*b doubles
+ *   d_x, d_y             device, n*b doubles each; must not alias
+ * Asynchronous.
+ */
+int bsr_spmv(int32_t n, int32_t b, const int32_t* d_row_ptr, const int32_t* d_col_idx,
+             const double* d_vals, const double* d_x, double* d_y, void* stream);
+
+/* ------------------------------------------------------------------------ */
+/* BiCGSTAB (device)                                                         */
+/* ------------------------------------------------------------------------ */
+
+typedef struct {
+  int32_t n;                /* block rows */
+  int32_t b;                /* block size */
+  const int32_t* row_ptr;   /* device, n+1 */
+  const int32_t* col_idx;   /* device, nnzb */
+  const double* vals;       /* device, nnzb*b*b, column-major blocks */
+} bilu_bsr;
+
+typedef struct {
+  int32_t status;           /* bilu_status of the solve */
+  int32_t iters;            /* BiCGSTAB iterations (a half iteration counts as one) */
+  double true_relres;       /* ||rhs - A x|| / ||rhs|| of the returned x */
+  double ms;                /* device time of the solve (CUDA events) */
+} bilu_solve_info;
+
+/* Scratch bytes bicgstab_solve needs (eight Krylov vectors, reductions and
+ * the apply workspace). */
+size_t bicgstab_workspace_bytes(const bilu_pattern* p, int32_t b);
+
+/*
+ * bicgstab_solve -- right-preconditioned BiCGSTAB (van der Vorst, as in the
+ * Templates book the paper cites) for A x = rhs with M = L D U' from
+ * bilu_factor:
+ *   r = rhs - A x0, r_hat = r;  each iteration: rho = (r_hat, r);
+ *   p = r + beta (p - omega v); p_hat = M^{-1} p; v = A p_hat;
+ *   alpha = rho / (r_hat, v); s = r - alpha v (stop if ||s||/||rhs|| <= tol);
+ *   s_hat = M^{-1} s; t = A s_hat; omega = (t, s)/(t, t);
+ *   x += alpha p_hat + omega s_hat; r = s - omega t.
+ * Convergence is declared when the recurrence residual drops below tol AND
+ * the recomputed true residual ||rhs - A x||/||rhs|| confirms it; otherwise
+ * the iteration restarts from the true residual until maxit is spent.
+ *   A          device matrix; A->n and A->b must match the pattern and b
+ *   d_factors  output of bilu_factor for the same pattern and b
+ *   d_rhs      device, n*b doubles
+ *   d_x        device, n*b doubles: x0 on entry, the solution on return
+ *   tol        relative residual target (> 0)
+ *   maxit      iteration limit (>= 0)
+ *   d_work     device scratch of at least bicgstab_workspace_bytes bytes
+ *   info       may be NULL
+ * Synchronises the stream a few times per iteration batch to test
+ * convergence.  Returns BILU_OK, BILU_ERR_NOT_CONVERGED, BILU_ERR_BREAKDOWN or
+ * BILU_ERR_TIMEOUT; x holds the last iterate in every case.
+ */
+int bicgstab_solve(const bilu_pattern* p, const bilu_bsr* A, const double* d_factors,
+                   const double* d_rhs, double* d_x, double tol, int32_t maxit, void* d_work,
+                   size_t work_bytes, void* stream, bilu_solve_info* info);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BILU_H */

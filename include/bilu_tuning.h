@@ -1,0 +1,78 @@
+/*
+ * bilu_tuning.h -- tuning knobs and test hooks of libbilu.  They change how
+ * the kernels of bilu.h are scheduled, never what they compute (the paper has
+ * no counterpart: these are implementation parameters).  Process-wide,
+ * host-side settings; not thread safe against concurrent calls.
+ */
+#ifndef BILU_TUNING_H
+#define BILU_TUNING_H
+
+#include <stdint.h>
+
+#include "bilu.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Consecutive block rows one CTA owns in the sync-free triangular solves
+ * (default 1024).  Dependencies inside a chunk resolve through shared memory,
+ * dependencies across chunks through global memory.  1 <= rows <= 2048, else
+ * BILU_ERR_ARG.  The per-chunk row order is rebuilt (host work plus one
+ * device allocation) by the next apply or solve on each pattern. */
+int bilu_set_trisolve_chunk(int32_t rows);
+int32_t bilu_get_trisolve_chunk(void);
+
+/* Host copy of the chunk-local row order the sync-free solves use for `rows`
+ * rows per chunk (the same order bilu_apply builds): chunk c occupies
+ * positions [c*rows, c*rows + len) of ord_lower (chunks of ascending rows) and
+ * of ord_upper (chunks of descending rows, starting from row n - 1); inside a
+ * chunk, rows are listed by their dependency level within the chunk.  Each
+ * output holds n entries (caller-allocated).  Host only. */
+int bilu_schedule_export(const bilu_pattern* p, int32_t rows, int32_t* ord_lower, int32_t* ord_upper);
+
+/* Time limit of every bounded dependency wait in the factorization and the
+ * triangular solves, in nanoseconds (default 2e9).  >= 1000, else
+ * BILU_ERR_ARG.  A wait that runs out records BILU_ERR_TIMEOUT and the kernel
+ * returns; it never traps. */
+int bilu_set_spin_limit_ns(int64_t ns);
+
+/* BiCGSTAB iterations enqueued between two host reads of the device state
+ * (default 4).  1 <= iters <= 1000, else BILU_ERR_ARG. */
+int bilu_set_check_every(int32_t iters);
+
+/* Test hook: the lower triangular solve computes block row `row` but never
+ * publishes it, so every row that depends on it waits until the spin limit
+ * and the call reports BILU_ERR_TIMEOUT.  -1 (the default) disables it. */
+int bilu_test_withhold_row(int32_t row);
+
+/* Kernel classes for bilu_profile_read. */
+enum bilu_prof_kernel {
+  BILU_PROF_SPMV = 0,         /* bsr_spmv kernel */
+  BILU_PROF_APPLY_PREP = 1,   /* apply: reset of the pending markers */
+  BILU_PROF_LOWER = 2,        /* apply: sync-free L y = r */
+  BILU_PROF_UPPER = 3,        /* apply: sync-free U' x = D^{-1} y */
+  BILU_PROF_BACKFILL = 4,     /* factor: A -> A' gather */
+  BILU_PROF_FACTOR = 5,       /* factor: Algorithm 4 + D^{-1} */
+  BILU_PROF_SCALE_UPPER = 6,  /* factor: U' = D^{-1} U */
+  BILU_PROF_KRYLOV = 7,       /* BiCGSTAB vector updates and reductions */
+  BILU_PROF_FACTOR_INIT = 8,  /* factor: reset of the ready flags */
+  BILU_PROF_NKERNELS = 9
+};
+
+/* Per-kernel timing: when on, every launch of the library is bracketed by
+ * CUDA events on its stream.  Enabling (or disabling) clears the counters. */
+int bilu_profile_enable(int32_t on);
+
+/* Waits for the recorded events and returns, for one kernel class, the
+ * number of timed launches and their summed device time in milliseconds. */
+int bilu_profile_read(int32_t kernel, int64_t* launches, double* total_ms);
+
+/* Number of kernels the library has launched in this process (all classes,
+ * whether or not profiling is on). */
+int64_t bilu_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

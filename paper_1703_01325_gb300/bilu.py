@@ -1,0 +1,241 @@
+"""Python face of libbilu: the same names as the C ABI, taking torch tensors.
+
+Argument marshalling only (dtype/device checks, pointer and stream
+extraction, buffer allocation through torch).  PyTorch provides device memory
+and streams; every step of the method runs in libbilu's CUDA kernels and its
+host symbolic phase.  Errors from the library raise ``BiluError``.
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+import torch
+
+from . import _lib as L
+
+
+class BiluError(RuntimeError):
+    def __init__(self, status: int, what: str, detail: str = ""):
+        msg = L.load().bilu_status_string(status).decode()
+        super().__init__(f"{what}: {msg} (status {status}){detail}")
+        self.status = status
+
+
+def _check(status: int, what: str, detail: str = ""):
+    if status != L.BILU_OK:
+        raise BiluError(status, what, detail)
+
+
+def _stream_handle(stream) -> C.c_void_p:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return C.c_void_p(stream.cuda_stream)
+
+
+def _dev(t: torch.Tensor, dtype, name: str) -> C.c_void_p:
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise ValueError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    return C.c_void_p(t.data_ptr())
+
+
+def _host_i32(a) -> np.ndarray:
+    if isinstance(a, torch.Tensor):
+        a = a.cpu().numpy()
+    return np.ascontiguousarray(a, dtype=np.int32)
+
+
+class Pattern:
+    """Library-owned level-of-fill pattern (handle from bilu_symbolic)."""
+
+    def __init__(self, handle: C.c_void_p):
+        self._h = handle
+        info = L.PatternInfo()
+        _check(L.load().bilu_pattern_query(self._h, C.byref(info)), "bilu_pattern_query")
+        self.info = info
+        self.uploaded = False
+
+    @property
+    def handle(self) -> C.c_void_p:
+        if self._h is None:
+            raise ValueError("pattern destroyed")
+        return self._h
+
+    @property
+    def n(self) -> int:
+        return self.info.n
+
+    def export(self):
+        """P' and the Eq. 4 levels as numpy arrays (bilu_pattern_export)."""
+        n, nnz = self.info.n, self.info.nnz_p
+        rp = np.zeros(n + 1, np.int32)
+        ci = np.zeros(max(nnz, 1), np.int32)
+        lev = np.zeros(max(nnz, 1), np.int32)
+        lo = np.zeros(max(n, 1), np.int32)
+        up = np.zeros(max(n, 1), np.int32)
+        p = lambda a: a.ctypes.data_as(C.POINTER(C.c_int32))
+        _check(L.load().bilu_pattern_export(self.handle, p(rp), p(ci), p(lev), p(lo), p(up)),
+               "bilu_pattern_export")
+        return dict(row_ptr=rp, col_idx=ci[:nnz], lev=lev[:nnz], lvl_lower=lo[:n], lvl_upper=up[:n])
+
+    def upload(self, stream=None):
+        _check(L.load().bilu_pattern_upload(self.handle, _stream_handle(stream)), "bilu_pattern_upload")
+        self.uploaded = True
+        return self
+
+    def schedule(self, rows: int):
+        """The chunk-local row orders of the sync-free solves (bilu_schedule_export)."""
+        n = self.info.n
+        lo = np.zeros(max(n, 1), np.int32)
+        up = np.zeros(max(n, 1), np.int32)
+        p = lambda a: a.ctypes.data_as(C.POINTER(C.c_int32))
+        _check(L.load().bilu_schedule_export(self.handle, rows, p(lo), p(up)), "bilu_schedule_export")
+        return lo[:n], up[:n]
+
+    def factor_bytes(self, b: int) -> int:
+        return int(L.load().bilu_factor_bytes(self.handle, b))
+
+    def factor_workspace_bytes(self, b: int) -> int:
+        return int(L.load().bilu_factor_workspace_bytes(self.handle, b))
+
+    def apply_workspace_bytes(self, b: int) -> int:
+        return int(L.load().bilu_apply_workspace_bytes(self.handle, b))
+
+    def bicgstab_workspace_bytes(self, b: int) -> int:
+        return int(L.load().bicgstab_workspace_bytes(self.handle, b))
+
+    def close(self):
+        if self._h is not None:
+            L.load().bilu_destroy_pattern(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def bilu_symbolic(n: int, row_ptr, col_idx, k: int) -> Pattern:
+    """Level-of-fill pattern P' of ILU(k) (host; Algorithm 3, Eq. 1-2, Eq. 4)."""
+    rp = _host_i32(row_ptr)
+    ci = _host_i32(col_idx)
+    if len(rp) != n + 1:
+        raise ValueError("row_ptr must hold n + 1 entries")
+    h = C.c_void_p()
+    p = lambda a: a.ctypes.data_as(C.POINTER(C.c_int32))
+    _check(L.load().bilu_symbolic(n, p(rp), p(ci) if len(ci) else None, k, C.byref(h)), "bilu_symbolic")
+    return Pattern(h)
+
+
+def workspace(nbytes: int, device=None) -> torch.Tensor:
+    """A device scratch buffer of at least nbytes bytes (torch allocation)."""
+    return torch.empty(max(int(nbytes), 256), dtype=torch.uint8,
+                       device=device if device is not None else "cuda")
+
+
+def new_factors(pattern: Pattern, b: int, device=None) -> torch.Tensor:
+    nb = pattern.factor_bytes(b)
+    return torch.empty(max(nb // 8, 1), dtype=torch.float64, device=device if device is not None else "cuda")
+
+
+def factor_sections(pattern: Pattern, b: int, factors: torch.Tensor):
+    """Views (L, Dinv, U') of a factor buffer, each shaped (blocks, b*b)."""
+    bb = b * b
+    nl, n, nu = pattern.info.nnz_l, pattern.info.n, pattern.info.nnz_u
+    f = factors[: (nl + n + nu) * bb].view(-1, bb) if (nl + n + nu) else factors[:0].view(0, bb)
+    return f[:nl], f[nl:nl + n], f[nl + n:nl + n + nu]
+
+
+def bilu_factor(pattern: Pattern, b: int, a_vals: torch.Tensor, factors: torch.Tensor | None = None,
+                work: torch.Tensor | None = None, stream=None, check: bool = True):
+    """Backfill + Algorithm 4 + Eq. 5 on the device.  Returns (factors, info)."""
+    if factors is None:
+        factors = new_factors(pattern, b, a_vals.device)
+    if work is None:
+        work = workspace(pattern.factor_workspace_bytes(b), a_vals.device)
+    info = L.FactorInfo()
+    st = L.load().bilu_factor(pattern.handle, b, _dev(a_vals, torch.float64, "a_vals"),
+                              _dev(factors, torch.float64, "factors"), _dev(work, torch.uint8, "work"),
+                              work.numel(), _stream_handle(stream), C.byref(info))
+    if check:
+        _check(st, "bilu_factor", f" (bad_row {info.bad_row})" if st == L.BILU_ERR_SINGULAR else "")
+    return factors, info
+
+
+def bilu_apply(pattern: Pattern, b: int, factors: torch.Tensor, r: torch.Tensor,
+               x: torch.Tensor | None = None, work: torch.Tensor | None = None, stream=None):
+    """x = (L D U')^{-1} r on the device (Eq. 6, Algorithm 7).  Asynchronous."""
+    if x is None:
+        x = torch.empty_like(r)
+    if work is None:
+        work = workspace(pattern.apply_workspace_bytes(b), r.device)
+    _check(L.load().bilu_apply(pattern.handle, b, _dev(factors, torch.float64, "factors"),
+                               _dev(r, torch.float64, "r"), _dev(x, torch.float64, "x"),
+                               _dev(work, torch.uint8, "work"), work.numel(), _stream_handle(stream)),
+           "bilu_apply")
+    return x
+
+
+def bilu_workspace_status(work: torch.Tensor, stream=None) -> int:
+    return L.load().bilu_workspace_status(_dev(work, torch.uint8, "work"), _stream_handle(stream))
+
+
+def bsr_spmv(n: int, b: int, row_ptr: torch.Tensor, col_idx: torch.Tensor, vals: torch.Tensor,
+             x: torch.Tensor, y: torch.Tensor | None = None, stream=None):
+    """y = A x for a block CSR matrix on the device.  Asynchronous."""
+    if y is None:
+        y = torch.empty_like(x)
+    _check(L.load().bsr_spmv(n, b, _dev(row_ptr, torch.int32, "row_ptr"), _dev(col_idx, torch.int32, "col_idx"),
+                             _dev(vals, torch.float64, "vals"), _dev(x, torch.float64, "x"),
+                             _dev(y, torch.float64, "y"), _stream_handle(stream)), "bsr_spmv")
+    return y
+
+
+def bicgstab_solve(pattern: Pattern, A, factors: torch.Tensor, rhs: torch.Tensor,
+                   x: torch.Tensor | None = None, tol: float = 1e-8, maxit: int = 1000,
+                   work: torch.Tensor | None = None, stream=None):
+    """Right-preconditioned BiCGSTAB on the device.  A = (n, b, row_ptr, col_idx,
+    vals) with device tensors.  Returns (x, info); info.status says whether it
+    converged (no exception for NOT_CONVERGED / BREAKDOWN / TIMEOUT)."""
+    n, b, rp, ci, vals = A
+    if x is None:
+        x = torch.zeros_like(rhs)
+    if work is None:
+        work = workspace(pattern.bicgstab_workspace_bytes(b), rhs.device)
+    bsr = L.BSR(n, b, _dev(rp, torch.int32, "row_ptr"), _dev(ci, torch.int32, "col_idx"),
+                _dev(vals, torch.float64, "vals"))
+    info = L.SolveInfo()
+    st = L.load().bicgstab_solve(pattern.handle, C.byref(bsr), _dev(factors, torch.float64, "factors"),
+                                 _dev(rhs, torch.float64, "rhs"), _dev(x, torch.float64, "x"), tol, maxit,
+                                 _dev(work, torch.uint8, "work"), work.numel(), _stream_handle(stream),
+                                 C.byref(info))
+    if st in (L.BILU_ERR_ARG, L.BILU_ERR_STATE, L.BILU_ERR_CUDA, L.BILU_ERR_OOM):
+        _check(st, "bicgstab_solve")
+    return x, info
+
+
+# ---- tuning / test hooks ----
+
+def bilu_set_trisolve_chunk(rows: int):
+    _check(L.load().bilu_set_trisolve_chunk(rows), "bilu_set_trisolve_chunk")
+
+
+def bilu_get_trisolve_chunk() -> int:
+    return int(L.load().bilu_get_trisolve_chunk())
+
+
+def bilu_set_spin_limit_ns(ns: int):
+    _check(L.load().bilu_set_spin_limit_ns(ns), "bilu_set_spin_limit_ns")
+
+
+def bilu_set_check_every(iters: int):
+    _check(L.load().bilu_set_check_every(iters), "bilu_set_check_every")
+
+
+def bilu_test_withhold_row(row: int):
+    _check(L.load().bilu_test_withhold_row(row), "bilu_test_withhold_row")

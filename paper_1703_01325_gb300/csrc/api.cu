@@ -1,0 +1,267 @@
+// api.cu -- C ABI entry points of libbilu (declared in include/bilu.h and
+// include/bilu_tuning.h): argument checks, the pattern's device copy, and the
+// stream-ordered launches of the kernels in spmv.cu, factor.cu, trisolve.cu and
+// krylov.cu.
+#include <cuda_runtime.h>
+
+#include <cstring>
+
+#include "../../include/bilu_tuning.h"
+#include "bilu_internal.h"
+
+using namespace bilu;
+
+namespace {
+
+bool valid_b(int32_t b) { return b >= 1 && b <= 8; }
+
+int ready(const bilu_pattern* p) {
+  if (!p) return BILU_ERR_ARG;
+  if (p->n > 0 && !p->d_mem) return BILU_ERR_STATE;
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) return BILU_ERR_CUDA;
+  if (p->n > 0 && dev != p->device) return BILU_ERR_STATE;
+  return BILU_OK;
+}
+
+int cuda_status(int e) { return e == 0 ? BILU_OK : BILU_ERR_CUDA; }
+
+}  // namespace
+
+extern "C" const char* bilu_status_string(int status) {
+  switch (status) {
+    case BILU_OK: return "ok";
+    case BILU_ERR_ARG: return "invalid argument";
+    case BILU_ERR_PATTERN: return "malformed block pattern (unsorted, duplicate or out-of-range column, or missing diagonal block)";
+    case BILU_ERR_SINGULAR: return "singular or non-finite pivot block";
+    case BILU_ERR_BREAKDOWN: return "BiCGSTAB breakdown";
+    case BILU_ERR_NOT_CONVERGED: return "iteration limit reached before the tolerance";
+    case BILU_ERR_TIMEOUT: return "a bounded dependency wait timed out";
+    case BILU_ERR_CUDA: return "CUDA runtime error";
+    case BILU_ERR_OOM: return "out of memory or size overflow";
+    case BILU_ERR_STATE: return "pattern not uploaded to this device, or workspace too small";
+    default: return "unknown status";
+  }
+}
+
+extern "C" int bilu_pattern_upload(bilu_pattern* p, void* stream) {
+  if (!p) return BILU_ERR_ARG;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return BILU_ERR_CUDA;
+  if (p->d_mem) {
+    cudaFree(p->d_mem);
+    p->d_mem = nullptr;
+  }
+  const int32_t n = p->n;
+  if (n == 0) {
+    p->device = dev;
+    return BILU_OK;
+  }
+  const size_t s_lrp = align256(sizeof(int32_t) * ((size_t)n + 1));
+  const size_t s_lci = align256(sizeof(int32_t) * (p->lci.size() + 1));
+  const size_t s_urp = s_lrp;
+  const size_t s_uci = align256(sizeof(int32_t) * (p->uci.size() + 1));
+  const size_t s_map = align256(sizeof(int32_t) * (p->slot_src.size() + 1));
+  const size_t total = s_lrp + s_lci + s_urp + s_uci + s_map;
+  void* mem = nullptr;
+  if (cudaMalloc(&mem, total) != cudaSuccess) {
+    cudaGetLastError();
+    return BILU_ERR_OOM;
+  }
+  char* c = (char*)mem;
+  p->d_lrp = (int32_t*)c; c += s_lrp;
+  p->d_lci = (int32_t*)c; c += s_lci;
+  p->d_urp = (int32_t*)c; c += s_urp;
+  p->d_uci = (int32_t*)c; c += s_uci;
+  p->d_slot_src = (int32_t*)c;
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaMemcpyAsync(p->d_lrp, p->lrp.data(), sizeof(int32_t) * ((size_t)n + 1), cudaMemcpyHostToDevice, s);
+  if (!p->lci.empty())
+    cudaMemcpyAsync(p->d_lci, p->lci.data(), sizeof(int32_t) * p->lci.size(), cudaMemcpyHostToDevice, s);
+  cudaMemcpyAsync(p->d_urp, p->urp.data(), sizeof(int32_t) * ((size_t)n + 1), cudaMemcpyHostToDevice, s);
+  if (!p->uci.empty())
+    cudaMemcpyAsync(p->d_uci, p->uci.data(), sizeof(int32_t) * p->uci.size(), cudaMemcpyHostToDevice, s);
+  cudaMemcpyAsync(p->d_slot_src, p->slot_src.data(), sizeof(int32_t) * p->slot_src.size(),
+                  cudaMemcpyHostToDevice, s);
+  if (cudaStreamSynchronize(s) != cudaSuccess) {
+    cudaFree(mem);
+    return BILU_ERR_CUDA;
+  }
+  p->d_mem = mem;
+  p->device = dev;
+  if (ensure_schedule(p, trisolve_config().chunk) != 0) return BILU_ERR_OOM;
+  return BILU_OK;
+}
+
+extern "C" void bilu_destroy_pattern(bilu_pattern* p) {
+  if (!p) return;
+  if (p->d_mem) cudaFree(p->d_mem);
+  if (p->d_sched) cudaFree(p->d_sched);
+  delete p;
+}
+
+extern "C" size_t bilu_factor_bytes(const bilu_pattern* p, int32_t b) {
+  if (!p || !valid_b(b)) return 0;
+  return (size_t)p->nslots() * b * b * sizeof(double);
+}
+
+extern "C" size_t bilu_factor_workspace_bytes(const bilu_pattern* p, int32_t b) {
+  if (!p || !valid_b(b)) return 0;
+  return kHeaderBytes + align256(sizeof(int32_t) * ((size_t)p->n + 1));
+}
+
+extern "C" int bilu_factor(const bilu_pattern* p, int32_t b, const double* d_a_vals,
+                           double* d_factors, void* d_work, size_t work_bytes, void* stream,
+                           bilu_factor_info* info) {
+  if (info) {
+    info->status = BILU_ERR_ARG;
+    info->bad_row = -1;
+    info->ms = 0.0;
+  }
+  if (!p || !valid_b(b)) return BILU_ERR_ARG;
+  int st = ready(p);
+  if (st) return st;
+  if (p->n > 0 && (!d_a_vals || !d_factors || !d_work)) return BILU_ERR_ARG;
+  if (work_bytes < bilu_factor_workspace_bytes(p, b)) return BILU_ERR_STATE;
+  if (ensure_schedule(const_cast<bilu_pattern*>(p), trisolve_config().chunk) != 0) return BILU_ERR_OOM;
+  cudaStream_t s = (cudaStream_t)stream;
+  int32_t* header = (int32_t*)d_work;
+  int32_t* done = (int32_t*)((char*)d_work + kHeaderBytes);
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  cudaEventRecord(e0, s);
+  int e = 0;
+  if (p->n > 0) e = launch_backfill(p, b, d_a_vals, d_factors, s);
+  if (!e) e = launch_factor(p, b, d_factors, header, done, s);
+  if (!e) e = launch_scale_upper(p, b, d_factors, s);
+  cudaEventRecord(e1, s);
+  int32_t hdr[kHeaderWords] = {0};
+  if (!e) e = (int)cudaMemcpyAsync(hdr, header, kHeaderBytes, cudaMemcpyDeviceToHost, s);
+  if (!e) e = (int)cudaStreamSynchronize(s);
+  float ms = 0.f;
+  if (!e) cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (e) return BILU_ERR_CUDA;
+  st = hdr[kErr];
+  if (info) {
+    info->status = st;
+    info->bad_row = (st == BILU_ERR_SINGULAR) ? hdr[kBadRow] : -1;
+    info->ms = ms;
+  }
+  return st;
+}
+
+extern "C" size_t bilu_apply_workspace_bytes(const bilu_pattern* p, int32_t b) {
+  if (!p || !valid_b(b)) return 0;
+  return apply_workspace_bytes(p->n, b);
+}
+
+extern "C" int bilu_apply(const bilu_pattern* p, int32_t b, const double* d_factors,
+                          const double* d_r, double* d_x, void* d_work, size_t work_bytes,
+                          void* stream) {
+  if (!p || !valid_b(b)) return BILU_ERR_ARG;
+  int st = ready(p);
+  if (st) return st;
+  if (p->n == 0) return BILU_OK;
+  if (!d_factors || !d_r || !d_x || !d_work || (const void*)d_r == (const void*)d_x) return BILU_ERR_ARG;
+  if (work_bytes < apply_workspace_bytes(p->n, b)) return BILU_ERR_STATE;
+  if (ensure_schedule(const_cast<bilu_pattern*>(p), trisolve_config().chunk) != 0) return BILU_ERR_OOM;
+  return cuda_status(launch_apply(p, b, d_factors, d_r, d_x, d_work, nullptr, stream));
+}
+
+extern "C" int bilu_workspace_status(const void* d_work, void* stream) {
+  if (!d_work) return BILU_ERR_ARG;
+  int err = 0;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (cudaMemcpyAsync(&err, (const int32_t*)d_work + kErr, sizeof(int), cudaMemcpyDeviceToHost, s) !=
+          cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return BILU_ERR_CUDA;
+  return err;
+}
+
+extern "C" int bsr_spmv(int32_t n, int32_t b, const int32_t* d_row_ptr, const int32_t* d_col_idx,
+                        const double* d_vals, const double* d_x, double* d_y, void* stream) {
+  if (n < 0 || !valid_b(b)) return BILU_ERR_ARG;
+  if (n == 0) return BILU_OK;
+  if (!d_row_ptr || !d_col_idx || !d_vals || !d_x || !d_y || (const void*)d_x == (const void*)d_y)
+    return BILU_ERR_ARG;
+  return cuda_status(launch_spmv(n, b, d_row_ptr, d_col_idx, d_vals, d_x, d_y, stream));
+}
+
+extern "C" size_t bicgstab_workspace_bytes(const bilu_pattern* p, int32_t b) {
+  if (!p || !valid_b(b)) return 0;
+  return krylov_workspace_bytes(p->n, b);
+}
+
+static int g_check_every = 4;
+
+extern "C" int bicgstab_solve(const bilu_pattern* p, const bilu_bsr* A, const double* d_factors,
+                              const double* d_rhs, double* d_x, double tol, int32_t maxit,
+                              void* d_work, size_t work_bytes, void* stream, bilu_solve_info* info) {
+  if (info) {
+    info->status = BILU_ERR_ARG;
+    info->iters = 0;
+    info->true_relres = 0.0;
+    info->ms = 0.0;
+  }
+  if (!p || !A || !valid_b(A->b) || A->n != p->n || !(tol > 0.0) || maxit < 0) return BILU_ERR_ARG;
+  int st = ready(p);
+  if (st) return st;
+  if (p->n == 0) {
+    if (info) info->status = BILU_OK;
+    return BILU_OK;
+  }
+  if (!A->row_ptr || !A->col_idx || !A->vals || !d_factors || !d_rhs || !d_x || !d_work ||
+      (const void*)d_rhs == (const void*)d_x)
+    return BILU_ERR_ARG;
+  if (work_bytes < krylov_workspace_bytes(p->n, A->b)) return BILU_ERR_STATE;
+  if (ensure_schedule(const_cast<bilu_pattern*>(p), trisolve_config().chunk) != 0) return BILU_ERR_OOM;
+  return run_bicgstab(p, A, d_factors, d_rhs, d_x, tol, maxit, d_work, stream, info, g_check_every);
+}
+
+// ---- tuning and test hooks (include/bilu_tuning.h) ----
+
+extern "C" int bilu_set_trisolve_chunk(int32_t rows) {
+  if (rows < 1 || rows > 2048) return BILU_ERR_ARG;
+  trisolve_config().chunk = rows;
+  return BILU_OK;
+}
+
+extern "C" int32_t bilu_get_trisolve_chunk(void) { return trisolve_config().chunk; }
+
+extern "C" int bilu_set_spin_limit_ns(int64_t ns) {
+  if (ns < 1000) return BILU_ERR_ARG;
+  trisolve_config().spin_ns = ns;
+  return BILU_OK;
+}
+
+extern "C" int bilu_set_check_every(int32_t iters) {
+  if (iters < 1 || iters > 1000) return BILU_ERR_ARG;
+  g_check_every = iters;
+  return BILU_OK;
+}
+
+extern "C" int bilu_test_withhold_row(int32_t row) {
+  trisolve_config().skip_row = row;
+  return BILU_OK;
+}
+
+extern "C" int bilu_schedule_export(const bilu_pattern* p, int32_t rows, int32_t* ord_lower,
+                                    int32_t* ord_upper) {
+  if (!p || rows < 1 || rows > 2048 || (p->n > 0 && (!ord_lower || !ord_upper))) return BILU_ERR_ARG;
+  bilu_pattern tmp;
+  tmp.n = p->n;
+  tmp.lrp = p->lrp;
+  tmp.lci = p->lci;
+  tmp.urp = p->urp;
+  tmp.uci = p->uci;
+  build_schedule(&tmp, rows);
+  if (p->n > 0) {
+    std::memcpy(ord_lower, tmp.ord_l.data(), sizeof(int32_t) * (size_t)p->n);
+    std::memcpy(ord_upper, tmp.ord_u.data(), sizeof(int32_t) * (size_t)p->n);
+  }
+  return BILU_OK;
+}

@@ -1,0 +1,110 @@
+// bilu_internal.h -- library-internal declarations shared by the host code and
+// the CUDA translation units of libbilu.  Not part of the C ABI.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <vector>
+
+#include "../../include/bilu.h"
+#include "../../include/bilu_tuning.h"
+
+struct bilu_pattern {
+  int32_t n = 0;
+  int32_t k = 0;
+  int64_t nnz_a = 0;
+  // P' (Algorithm 3 output): CSR with the level of fill of every entry.
+  std::vector<int32_t> rp, ci, lev;
+  // Eq. 4 dependency levels (0-based).
+  std::vector<int32_t> lvl_l, lvl_u;
+  int32_t nlev_l = 0, nlev_u = 0;
+  // Strictly lower / strictly upper parts of P' as separate CSR structures.
+  std::vector<int32_t> lrp, lci, urp, uci;
+  // Backfill gather map: for every factor slot in [L | D | U] the A block that
+  // lands there, or -1 for a fill block (Algorithm 5 steps 3-4).
+  std::vector<int32_t> slot_src;
+  // Sync-free solve schedule (see trisolve.cu): rows cut into chunks of
+  // sched_chunk consecutive rows (ascending chunks for L, descending for U');
+  // ord_l / ord_u list each chunk's rows by local dependency level.
+  int32_t sched_chunk = 0;
+  std::vector<int32_t> ord_l, ord_u;
+  void* d_sched = nullptr;
+  int32_t* d_ord_l = nullptr;
+  int32_t* d_ord_u = nullptr;
+  // Device copy (bilu_pattern_upload).
+  int device = -1;
+  void* d_mem = nullptr;
+  int32_t* d_lrp = nullptr;
+  int32_t* d_lci = nullptr;
+  int32_t* d_urp = nullptr;
+  int32_t* d_uci = nullptr;
+  int32_t* d_slot_src = nullptr;
+
+  int64_t nnz_l() const { return (int64_t)lci.size(); }
+  int64_t nnz_u() const { return (int64_t)uci.size(); }
+  int64_t nslots() const { return nnz_l() + n + nnz_u(); }
+};
+
+namespace bilu {
+
+// Workspace header: 64 32-bit words at the start of every workspace.
+enum HeaderWord : int {
+  kTicketL = 0,   // chunk ticket of the lower solve
+  kTicketU = 1,   // chunk ticket of the upper solve
+  kTicketF = 2,   // row ticket of the factorization
+  kErr = 3,       // first device error (bilu_status), 0 = none
+  kAbort = 4,     // set once any bounded wait gave up: every waiter leaves
+  kBadRow = 5,    // smallest singular row (INT32_MAX = none)
+  kHeaderWords = 64
+};
+constexpr size_t kHeaderBytes = kHeaderWords * 4;
+
+inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// Default spin limit of a dependency wait, in nanoseconds of %globaltimer.
+constexpr long long kDefaultSpinNs = 2000000000LL;  // 2 s
+
+// Tunables of the sync-free triangular solves (see trisolve.cu).
+struct TrisolveConfig {
+  int chunk = 1024;        // consecutive block rows processed by one CTA
+  long long spin_ns = kDefaultSpinNs;
+  int skip_row = -1;       // test hook: this row of the lower solve is never published
+};
+TrisolveConfig& trisolve_config();
+
+// Brackets one kernel launch with profiling events (when enabled) and counts it.
+class ProfScope {
+ public:
+  ProfScope(int id, void* stream);
+  ~ProfScope();
+  ProfScope(const ProfScope&) = delete;
+  ProfScope& operator=(const ProfScope&) = delete;
+
+ private:
+  int id_;
+  void* stream_;
+  void* a_;
+};
+
+// ---- kernels (launchers return cudaError_t as int) ----
+int launch_spmv(int32_t n, int32_t b, const int32_t* rp, const int32_t* ci, const double* vals,
+                const double* x, double* y, void* stream, const int32_t* stop = nullptr);
+
+int launch_backfill(const bilu_pattern* p, int32_t b, const double* a_vals, double* f, void* stream);
+int launch_factor(const bilu_pattern* p, int32_t b, double* f, int32_t* header, int32_t* done,
+                  void* stream);
+int launch_scale_upper(const bilu_pattern* p, int32_t b, double* f, void* stream);
+
+size_t apply_workspace_bytes(int32_t n, int32_t b);
+// Builds (host) and uploads the solve schedule for `chunk` rows per chunk.
+int ensure_schedule(bilu_pattern* p, int32_t chunk);
+void build_schedule(bilu_pattern* p, int32_t chunk);  // host part (symbolic.cpp)
+int launch_apply(const bilu_pattern* p, int32_t b, const double* f, const double* r, double* x,
+                 void* work, int32_t* stop, void* stream);
+
+size_t krylov_workspace_bytes(int32_t n, int32_t b);
+int run_bicgstab(const bilu_pattern* p, const bilu_bsr* A, const double* f, const double* rhs,
+                 double* x, double tol, int32_t maxit, void* work, void* stream,
+                 bilu_solve_info* info, int batch);
+
+}  // namespace bilu

@@ -1,0 +1,137 @@
+// device_common.cuh -- device helpers shared by the libbilu kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "bilu_internal.h"
+
+namespace bilu {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+// "Not yet computed" marker of the sync-free triangular solves: a signalling
+// NaN with a fixed payload.  IEEE arithmetic quiets every signalling NaN it
+// touches, so no computed value carries this bit pattern; a stored value that
+// would (a copied input) is replaced by a quiet NaN first.
+constexpr unsigned long long kPending = 0x7FF4DEADBEEF0001ull;
+constexpr unsigned long long kQuietNaN = 0x7FF8000000000000ull;
+
+__device__ __forceinline__ unsigned long long ld_relaxed_u64(const void* p) {
+  unsigned long long v;
+  asm volatile("ld.relaxed.gpu.global.b64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_relaxed_u64(void* p, unsigned long long v) {
+  asm volatile("st.relaxed.gpu.global.b64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ int ld_acquire_s32(const int* p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release_s32(int* p, int v) {
+  asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ int ld_volatile_s32(const int* p) {
+  return *reinterpret_cast<const volatile int*>(p);
+}
+__device__ __forceinline__ long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return (long long)t;
+}
+
+// Publish one computed value for the sync-free solves.
+__device__ __forceinline__ void publish(double* p, double v) {
+  unsigned long long u = (unsigned long long)__double_as_longlong(v);
+  if (u == kPending) u = kQuietNaN;
+  st_relaxed_u64(p, u);
+}
+
+// Bounded wait state: the first waiter that runs out of time records
+// BILU_ERR_TIMEOUT and raises the abort word so that every other waiter
+// leaves promptly.  No waiter ever traps.
+struct Waiter {
+  int* header;
+  long long limit_ns;
+  long long t0;
+  int* stop_word;  // optional: raised too, so a caller's pipeline stops
+  __device__ __forceinline__ bool give_up(unsigned it) {
+    if ((it & 31u) != 0u) return false;
+    if (ld_volatile_s32(header + kAbort)) return true;
+    if (t0 == 0) t0 = global_ns();
+    if (global_ns() - t0 > limit_ns) {
+      atomicCAS(header + kErr, 0, (int)BILU_ERR_TIMEOUT);
+      atomicExch(header + kAbort, 1);
+      if (stop_word) atomicExch(stop_word, 1);
+      return true;
+    }
+    return false;
+  }
+};
+
+// Wait until *p holds a computed value; false if the wait was abandoned.
+__device__ __forceinline__ bool wait_value(const double* p, double& out, Waiter& w) {
+  w.t0 = 0;  // the time limit applies to each wait separately
+  for (unsigned it = 1;; ++it) {
+    unsigned long long u = ld_relaxed_u64(p);
+    if (u != kPending) {
+      out = __longlong_as_double((long long)u);
+      return true;
+    }
+    if (w.give_up(it)) return false;
+  }
+}
+
+// Wait until *flag != 0 (acquire); false if the wait was abandoned.
+__device__ __forceinline__ bool wait_flag(const int* flag, Waiter& w) {
+  w.t0 = 0;
+  for (unsigned it = 1;; ++it) {
+    if (ld_acquire_s32(flag) != 0) return true;
+    if (w.give_up(it)) return false;
+  }
+}
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) {
+  return (unsigned)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ int ld_acquire_cta_shared_s32(const int* p) {
+  int v;
+  asm volatile("ld.acquire.cta.shared.b32 %0, [%1];" : "=r"(v) : "r"(smem_u32(p)) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release_cta_shared_s32(int* p, int v) {
+  asm volatile("st.release.cta.shared.b32 [%0], %1;" ::"r"(smem_u32(p)), "r"(v) : "memory");
+}
+
+// Wait until a shared-memory flag of this CTA equals `want` (acquire, CTA
+// scope); false if the wait was abandoned.
+__device__ __forceinline__ bool wait_local_flag(const int* flag, int want, Waiter& w) {
+  w.t0 = 0;
+  for (unsigned it = 1;; ++it) {
+    if (ld_acquire_cta_shared_s32(flag) == want) return true;
+    if (w.give_up(it)) return false;
+  }
+}
+
+// Lanes per output-component group for a b x b block in a 32-lane warp: the
+// largest power of two G with G*b <= 32.
+__host__ __device__ constexpr int groups_for(int b) {
+  return b == 1 ? 32 : b == 2 ? 16 : b <= 4 ? 8 : 4;
+}
+
+}  // namespace bilu
+
+#define BILU_DISPATCH_B(b, ...)                  \
+  switch (b) {                                   \
+    case 1: { constexpr int B = 1; __VA_ARGS__; } break; \
+    case 2: { constexpr int B = 2; __VA_ARGS__; } break; \
+    case 3: { constexpr int B = 3; __VA_ARGS__; } break; \
+    case 4: { constexpr int B = 4; __VA_ARGS__; } break; \
+    case 5: { constexpr int B = 5; __VA_ARGS__; } break; \
+    case 6: { constexpr int B = 6; __VA_ARGS__; } break; \
+    case 7: { constexpr int B = 7; __VA_ARGS__; } break; \
+    case 8: { constexpr int B = 8; __VA_ARGS__; } break; \
+    default: break;                              \
+  }

@@ -1,0 +1,68 @@
+// spmv.cu -- block CSR SpMV y = A x (the SpMV of Section 2.4 / Algorithm 7).
+//
+// One lane per output component: a warp owns R = floor(32 / b) consecutive
+// block rows and lane (row, r) accumulates y[row][r] = sum_t sum_c
+// A_t[r][c] x_{col(t)}[c] over the row's blocks in column order.  Each lane
+// does exactly b FMAs per block, so the FP64 pipe (the scarce unit on this part)
+// does no reduction work; the b lanes of a row read b consecutive doubles of
+// each block column, and the R rows of a warp are consecutive in memory, so
+// every byte of the warp's contiguous value range is used.  Values are
+// streamed with cache-streaming loads; x stays in L2 for the gathers.
+#include <cuda_runtime.h>
+
+#include "device_common.cuh"
+
+namespace bilu {
+namespace {
+
+// Streaming load (cache-streaming: evict-first in L1 and L2).
+__device__ __forceinline__ double ld_stream(const double* p) { return __ldcs(p); }
+
+template <int B>
+__global__ void __launch_bounds__(256) spmv_kernel(int32_t n, const int32_t* __restrict__ rp,
+                                                   const int32_t* __restrict__ ci,
+                                                   const double* __restrict__ vals,
+                                                   const double* __restrict__ x,
+                                                   double* __restrict__ y,
+                                                   const int32_t* stop) {
+  constexpr int R = 32 / B;
+  if (stop && ld_volatile_s32(stop)) return;
+  const int lane = threadIdx.x & 31;
+  const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int q = lane / B;
+  const int r = lane - q * B;
+  const long long row = warp * R + q;
+  if (q >= R || row >= n) return;
+  const int32_t beg = rp[row], end = rp[row + 1];
+  double acc = 0.0;
+  for (int32_t t = beg; t < end; ++t) {
+    const int32_t j = __ldg(ci + t);
+    const double* a = vals + (size_t)t * (B * B) + r;
+    const double* xj = x + (size_t)j * B;
+    double av[B];
+#pragma unroll
+    for (int c = 0; c < B; ++c) av[c] = ld_stream(a + c * B);
+#pragma unroll
+    for (int c = 0; c < B; ++c) acc = fma(av[c], __ldg(xj + c), acc);
+  }
+  y[row * B + r] = acc;
+}
+
+}  // namespace
+
+int launch_spmv(int32_t n, int32_t b, const int32_t* rp, const int32_t* ci, const double* vals,
+                const double* x, double* y, void* stream, const int32_t* stop) {
+  if (n == 0) return 0;
+  cudaStream_t s = (cudaStream_t)stream;
+  BILU_DISPATCH_B(b, {
+    constexpr int R = 32 / B;
+    const long long warps = ((long long)n + R - 1) / R;
+    const int tpb = 256;
+    const long long blocks = (warps * 32 + tpb - 1) / tpb;
+    ProfScope ps(BILU_PROF_SPMV, stream);
+    spmv_kernel<B><<<(unsigned)blocks, tpb, 0, s>>>(n, rp, ci, vals, x, y, stop);
+  });
+  return (int)cudaGetLastError();
+}
+
+}  // namespace bilu

@@ -1,0 +1,259 @@
+// symbolic.cpp -- host symbolic phase of the block ILU(k) library.
+//
+// Section 2.3: the block matrix is abstracted to its block graph (every listed
+// block is one point, whatever its values).  Section 2.2, Algorithm 3 with
+// Eq. 1 and Eq. 2 gives the level-of-fill pattern P'; Section 2.4, Eq. 4 gives
+// the dependency levels of the two triangular solves.  Everything here depends
+// on the pattern only, never on values, which is what lets the factorization
+// reuse it (the decoupling argument of Section 1).
+//
+// Row i is built by a pivot-driven merge: a min-heap releases the pivots
+// p < i of row i in ascending column order (each pivot's level is final when it
+// leaves the heap, because only smaller pivots can lower it), and every pivot
+// of level <= k offers lev_ip + lev_pj + 1 to the columns j > p of P'(p)
+// (Eq. 2).  Candidates above k are discarded at once: a level only decreases,
+// so such a candidate could never survive the final lev <= k test.
+
+#include <algorithm>
+#include <climits>
+#include <cstring>
+#include <functional>
+#include <new>
+#include <queue>
+#include <vector>
+
+#include "bilu_internal.h"
+
+namespace {
+
+int check_pattern(int32_t n, const int32_t* rp, const int32_t* ci) {
+  if (n < 0) return BILU_ERR_ARG;
+  if (n == 0) return BILU_OK;
+  if (!rp || (rp[n] > 0 && !ci)) return BILU_ERR_ARG;
+  if (rp[0] != 0) return BILU_ERR_PATTERN;
+  for (int32_t i = 0; i < n; ++i) {
+    if (rp[i + 1] < rp[i]) return BILU_ERR_PATTERN;
+    bool diag = false;
+    for (int32_t t = rp[i]; t < rp[i + 1]; ++t) {
+      const int32_t j = ci[t];
+      if (j < 0 || j >= n) return BILU_ERR_PATTERN;
+      if (t > rp[i] && j <= ci[t - 1]) return BILU_ERR_PATTERN;
+      diag |= (j == i);
+    }
+    if (!diag) return BILU_ERR_PATTERN;
+  }
+  return BILU_OK;
+}
+
+}  // namespace
+
+extern "C" int bilu_symbolic(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, int32_t k,
+                             bilu_pattern** out) {
+  if (!out || k < 0) return BILU_ERR_ARG;
+  *out = nullptr;
+  int st = check_pattern(n, row_ptr, col_idx);
+  if (st != BILU_OK) return st;
+  bilu_pattern* p = new (std::nothrow) bilu_pattern();
+  if (!p) return BILU_ERR_OOM;
+  try {
+    p->n = n;
+    p->k = k;
+    p->nnz_a = n > 0 ? row_ptr[n] : 0;
+    p->rp.assign((size_t)n + 1, 0);
+    p->ci.reserve((size_t)p->nnz_a * 2 + 16);
+    p->lev.reserve((size_t)p->nnz_a * 2 + 16);
+
+    std::vector<int32_t> mark((size_t)n, -1);   // mark[j] == i: column j is in row i
+    std::vector<int32_t> level((size_t)n, 0);   // level of column j in the current row
+    std::vector<int32_t> cols;
+    std::priority_queue<int32_t, std::vector<int32_t>, std::greater<int32_t>> pivots;
+
+    for (int32_t i = 0; i < n; ++i) {
+      cols.clear();
+      for (int32_t t = row_ptr[i]; t < row_ptr[i + 1]; ++t) {  // Eq. 1
+        const int32_t j = col_idx[t];
+        mark[j] = i;
+        level[j] = 0;
+        cols.push_back(j);
+        if (j < i) pivots.push(j);
+      }
+      while (!pivots.empty()) {
+        const int32_t piv = pivots.top();
+        pivots.pop();
+        const int64_t lp = level[piv];
+        if (lp > k) continue;
+        for (int32_t t = p->rp[piv]; t < p->rp[piv + 1]; ++t) {
+          const int32_t j = p->ci[t];
+          if (j <= piv) continue;
+          const int64_t cand = lp + p->lev[t] + 1;  // Eq. 2
+          if (cand > k) continue;
+          if (mark[j] != i) {
+            mark[j] = i;
+            level[j] = (int32_t)cand;
+            cols.push_back(j);
+            if (j < i) pivots.push(j);
+          } else if (cand < level[j]) {
+            level[j] = (int32_t)cand;
+          }
+        }
+      }
+      std::sort(cols.begin(), cols.end());
+      if ((int64_t)p->ci.size() + (int64_t)cols.size() > (int64_t)INT32_MAX) {
+        delete p;
+        return BILU_ERR_OOM;
+      }
+      for (int32_t j : cols) {
+        p->ci.push_back(j);
+        p->lev.push_back(level[j]);
+      }
+      p->rp[(size_t)i + 1] = (int32_t)p->ci.size();
+    }
+
+    // Eq. 4 on the lower part (rows ascending) and on the reversed graph of the
+    // upper part (rows descending); 0-based.
+    p->lvl_l.assign((size_t)n, 0);
+    p->lvl_u.assign((size_t)n, 0);
+    int32_t ml = -1, mu = -1;
+    for (int32_t i = 0; i < n; ++i) {
+      int32_t l = 0;
+      for (int32_t t = p->rp[i]; t < p->rp[i + 1] && p->ci[t] < i; ++t)
+        l = std::max(l, p->lvl_l[p->ci[t]] + 1);
+      p->lvl_l[i] = l;
+      ml = std::max(ml, l);
+    }
+    for (int32_t i = n - 1; i >= 0; --i) {
+      int32_t l = 0;
+      for (int32_t t = p->rp[i + 1] - 1; t >= p->rp[i] && p->ci[t] > i; --t)
+        l = std::max(l, p->lvl_u[p->ci[t]] + 1);
+      p->lvl_u[i] = l;
+      mu = std::max(mu, l);
+    }
+    p->nlev_l = ml + 1;
+    p->nlev_u = mu + 1;
+
+    // Split P' into strictly lower and strictly upper CSR structures.
+    p->lrp.assign((size_t)n + 1, 0);
+    p->urp.assign((size_t)n + 1, 0);
+    for (int32_t i = 0; i < n; ++i) {
+      int32_t nl = 0, nu = 0;
+      for (int32_t t = p->rp[i]; t < p->rp[i + 1]; ++t) {
+        if (p->ci[t] < i) ++nl;
+        else if (p->ci[t] > i) ++nu;
+      }
+      p->lrp[(size_t)i + 1] = p->lrp[i] + nl;
+      p->urp[(size_t)i + 1] = p->urp[i] + nu;
+    }
+    p->lci.resize((size_t)p->lrp[n]);
+    p->uci.resize((size_t)p->urp[n]);
+    for (int32_t i = 0; i < n; ++i) {
+      int32_t a = p->lrp[i], c = p->urp[i];
+      for (int32_t t = p->rp[i]; t < p->rp[i + 1]; ++t) {
+        if (p->ci[t] < i) p->lci[a++] = p->ci[t];
+        else if (p->ci[t] > i) p->uci[c++] = p->ci[t];
+      }
+    }
+
+    // Backfill gather map (Algorithm 5 steps 3-4): slot -> A block or -1.
+    const int64_t nl = p->nnz_l(), nslots = p->nslots();
+    if (nslots > (int64_t)INT32_MAX) {
+      delete p;
+      return BILU_ERR_OOM;
+    }
+    p->slot_src.assign((size_t)nslots, -1);
+    for (int32_t i = 0; i < n; ++i) {
+      int32_t a = p->lrp[i], c = p->urp[i];
+      for (int32_t t = row_ptr[i]; t < row_ptr[i + 1]; ++t) {
+        const int32_t j = col_idx[t];
+        int64_t slot;
+        if (j < i) {
+          while (p->lci[a] != j) ++a;  // A's pattern is a subset of P'
+          slot = a;
+        } else if (j == i) {
+          slot = nl + i;
+        } else {
+          while (p->uci[c] != j) ++c;
+          slot = nl + n + c;
+        }
+        p->slot_src[(size_t)slot] = t;
+      }
+    }
+  } catch (const std::bad_alloc&) {
+    delete p;
+    return BILU_ERR_OOM;
+  }
+  *out = p;
+  return BILU_OK;
+}
+
+extern "C" int bilu_pattern_query(const bilu_pattern* p, bilu_pattern_info* info) {
+  if (!p || !info) return BILU_ERR_ARG;
+  info->n = p->n;
+  info->k = p->k;
+  info->nnz_a = p->nnz_a;
+  info->nnz_p = (int64_t)p->ci.size();
+  info->nnz_l = p->nnz_l();
+  info->nnz_u = p->nnz_u();
+  info->nlev_l = p->nlev_l;
+  info->nlev_u = p->nlev_u;
+  return BILU_OK;
+}
+
+extern "C" int bilu_pattern_export(const bilu_pattern* p, int32_t* row_ptr, int32_t* col_idx,
+                                   int32_t* lev, int32_t* lvl_lower, int32_t* lvl_upper) {
+  if (!p) return BILU_ERR_ARG;
+  const size_t n = (size_t)p->n, nnz = p->ci.size();
+  if (row_ptr) std::memcpy(row_ptr, p->rp.data(), sizeof(int32_t) * (n + 1));
+  if (col_idx && nnz) std::memcpy(col_idx, p->ci.data(), sizeof(int32_t) * nnz);
+  if (lev && nnz) std::memcpy(lev, p->lev.data(), sizeof(int32_t) * nnz);
+  if (lvl_lower && n) std::memcpy(lvl_lower, p->lvl_l.data(), sizeof(int32_t) * n);
+  if (lvl_upper && n) std::memcpy(lvl_upper, p->lvl_u.data(), sizeof(int32_t) * n);
+  return BILU_OK;
+}
+
+namespace bilu {
+
+// Chunk-local dependency order of the sync-free triangular solves.  Rows are
+// cut into chunks of `chunk` consecutive rows; the lower solve takes chunks in
+// ascending order, the upper solve in descending order.  Inside a chunk, the
+// local level of a row is 1 + the largest local level of the rows of the same
+// chunk it depends on (0 if none), i.e. Eq. 4 restricted to the chunk; rows
+// are listed by (local level, row) for L and (local level, descending row) for
+// U'.  Chunk c occupies positions [c*chunk, c*chunk + len) of ord_l / ord_u.
+void build_schedule(bilu_pattern* p, int32_t chunk) {
+  const int32_t n = p->n;
+  p->ord_l.assign((size_t)n, 0);
+  p->ord_u.assign((size_t)n, 0);
+  std::vector<int32_t> loc((size_t)std::max(chunk, 1), 0);
+  std::vector<std::pair<int32_t, int32_t>> key;
+  const int32_t nchunks = (n + chunk - 1) / chunk;
+  for (int32_t c = 0; c < nchunks; ++c) {
+    // lower: rows [lo, hi)
+    int32_t lo = c * chunk, hi = std::min(n, lo + chunk);
+    key.clear();
+    for (int32_t i = lo; i < hi; ++i) {
+      int32_t l = 0;
+      for (int32_t t = p->lrp[i]; t < p->lrp[i + 1]; ++t)
+        if (p->lci[t] >= lo) l = std::max(l, loc[p->lci[t] - lo] + 1);
+      loc[i - lo] = l;
+      key.emplace_back(l, i);
+    }
+    std::sort(key.begin(), key.end());
+    for (size_t q = 0; q < key.size(); ++q) p->ord_l[(size_t)c * chunk + q] = key[q].second;
+    // upper: rows [lo, hi) with hi = n - c*chunk
+    hi = n - c * chunk;
+    lo = std::max(0, hi - chunk);
+    key.clear();
+    for (int32_t i = hi - 1; i >= lo; --i) {
+      int32_t l = 0;
+      for (int32_t t = p->urp[i]; t < p->urp[i + 1]; ++t)
+        if (p->uci[t] < hi) l = std::max(l, loc[p->uci[t] - lo] + 1);
+      loc[i - lo] = l;
+      key.emplace_back(l, -i);
+    }
+    std::sort(key.begin(), key.end());
+    for (size_t q = 0; q < key.size(); ++q) p->ord_u[(size_t)c * chunk + q] = -key[q].second;
+  }
+  p->sched_chunk = chunk;
+}
+
+}  // namespace bilu

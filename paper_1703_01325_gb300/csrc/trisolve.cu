@@ -1,0 +1,332 @@
+// trisolve.cu -- preconditioner apply x = M^{-1} r, M = L D U' (Eq. 6,
+// Algorithm 7): L y = r, then U' x = D^{-1} y with the D^{-1} product fused
+// into the upper solve (row i forms D_i^{-1} y_i and subtracts U'_ij x_j).
+//
+// The paper schedules each triangular solve by dependency levels (Eq. 4,
+// Algorithm 6), one parallel step per level.  On this part a dependent launch
+// costs >= 0.7 us and a dependency crossing SMs about 0.5 us, while a
+// 128x128x64 ILU(1) factor has 571 levels, so each solve is ONE sync-free
+// kernel with two tiers of dependency tracking instead:
+//  * block rows are cut into chunks of consecutive rows; CTAs claim chunks in
+//    solve order (ascending for L, descending for U') through an atomic
+//    ticket;
+//  * inside a chunk the host lists the rows by local dependency level (Eq. 4
+//    restricted to the chunk); the CTA's warps take rows round-robin in that
+//    order, and a dependency inside the chunk is read from shared memory after
+//    an acquire on the row's shared-memory ready flag (release by the writing
+//    lane): a hop of tens of nanoseconds.  In natural order most dependencies
+//    of a grid row lie within a few grid lines, i.e. inside its chunk;
+//  * a dependency outside the chunk is read from global memory, waiting until
+//    it no longer holds the "pending" bit pattern: the value is its own ready
+//    flag (no separate flag, no fence, one L2 round trip);
+//  * the column indices and values of a warp's next row are loaded into
+//    registers before the current row's waits start;
+//  * forward progress: a row only waits on rows of earlier positions in its
+//    chunk or of earlier tickets, all held by running warps; every wait is
+//    bounded and gives up with BILU_ERR_TIMEOUT (never a trap), and no warp
+//    leaves the CTA's chunk loop early, so no barrier can hang.
+// Lane mapping inside a row: lane = g*B + r, r the output component, g one of
+// G groups that take the row's blocks round-robin; each lane does B FMAs per
+// block and a log2(G)-step shuffle tree sums the groups.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
+#include "device_common.cuh"
+
+namespace bilu {
+
+TrisolveConfig& trisolve_config() {
+  static TrisolveConfig cfg;
+  return cfg;
+}
+
+namespace {
+
+constexpr int kTriWarps = 8;
+
+__global__ void apply_prep_kernel(double* y, long long m, int32_t* header, const int32_t* stop) {
+  // Each apply starts with a clean header: its status is its own.
+  if (stop && *stop) return;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < m; q += stride)
+    reinterpret_cast<unsigned long long*>(y)[q] = kPending;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    header[kTicketL] = 0;
+    header[kTicketU] = 0;
+    header[kAbort] = 0;
+    header[kErr] = 0;
+  }
+}
+
+// Registers a lane holds for one row: the row, its first block of this lane's
+// group (column and this lane's B values), and what the row's own update
+// needs (r_i for L; D_i^{-1} row and y_i for U').
+template <int B, bool UPPER>
+struct RowPre {
+  int i, beg, end, j;
+  double av[B];
+  double own;       // L: r_i[lane]
+  double d[B];      // U': D_i^{-1}[lane][q]
+  double yi[B];     // U': y_i[q]
+};
+
+template <int B, bool UPPER>
+__device__ __forceinline__ void fetch_row(RowPre<B, UPPER>& p, int pos, int len, const int* s_i,
+                                          const int* s_beg, const int* s_end,
+                                          const int32_t* __restrict__ ci,
+                                          const double* __restrict__ vals,
+                                          const double* __restrict__ dinv, const double* rhs,
+                                          int g, int rr, bool act, int lane) {
+  if (pos >= len) {
+    p.i = -1;
+    p.beg = p.end = 0;
+    return;
+  }
+  p.i = s_i[pos];
+  p.beg = s_beg[pos];
+  p.end = s_end[pos];
+  const int t = p.beg + g;
+  p.j = -1;
+  if (act && t < p.end) {
+    p.j = __ldg(ci + t);
+    const double* a = vals + (size_t)t * (B * B) + rr;
+#pragma unroll
+    for (int q = 0; q < B; ++q) p.av[q] = __ldg(a + q * B);
+  }
+  if (lane < B) {
+    if (!UPPER) {
+      p.own = rhs[(size_t)p.i * B + lane];
+    } else {
+      const double* di = dinv + (size_t)p.i * (B * B) + lane;
+#pragma unroll
+      for (int q = 0; q < B; ++q) {
+        p.d[q] = __ldg(di + q * B);
+        p.yi[q] = rhs[(size_t)p.i * B + q];
+      }
+    }
+  }
+}
+
+template <int B, bool UPPER>
+__global__ void __launch_bounds__(kTriWarps * 32) tri_solve_kernel(
+    int32_t n, int32_t chunk, int32_t nchunks, const int32_t* __restrict__ rp,
+    const int32_t* __restrict__ ci, const double* __restrict__ vals,
+    const double* __restrict__ dinv, const int32_t* __restrict__ ord, const double* rhs,
+    double* out, double* pend_out, int32_t* header, long long spin_ns, int32_t skip_row,
+    int32_t* stop) {
+  constexpr int G = groups_for(B);
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double* yl = reinterpret_cast<double*>(smem_raw);
+  int* fl = reinterpret_cast<int*>(yl + (size_t)chunk * B);
+  int* s_i = fl + chunk;
+  int* s_beg = s_i + chunk;
+  int* s_end = s_beg + chunk;
+  __shared__ int s_c;
+  if (stop && ld_volatile_s32(stop)) return;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int g = lane / B, rr = lane - (lane / B) * B;
+  const bool act = g < G;
+  for (int q = tid; q < chunk; q += blockDim.x) fl[q] = -1;
+  Waiter w{header, spin_ns, 0, stop};
+  bool dead = false;
+  for (;;) {
+    __syncthreads();  // the previous chunk is complete: shared memory may be reused
+    if (tid == 0) {
+      int cc = atomicAdd(header + (UPPER ? kTicketU : kTicketL), 1);
+      if (ld_volatile_s32(header + kAbort)) cc = nchunks;
+      s_c = cc;
+    }
+    __syncthreads();
+    const int c = s_c;
+    if (c >= nchunks) return;
+    int lo, hi;
+    if (!UPPER) {
+      lo = c * chunk;
+      hi = min(lo + chunk, n);
+    } else {
+      hi = n - c * chunk;
+      lo = max(hi - chunk, 0);
+    }
+    const int len = hi - lo;
+    const int base = c * chunk;
+    for (int q = tid; q < len; q += blockDim.x) {
+      const int i = ord[base + q];
+      s_i[q] = i;
+      s_beg[q] = rp[i];
+      s_end[q] = rp[i + 1];
+    }
+    __syncthreads();
+    RowPre<B, UPPER> cur, nxt;
+    fetch_row<B, UPPER>(cur, warp, len, s_i, s_beg, s_end, ci, vals, dinv, rhs, g, rr, act, lane);
+    for (int pos = warp; pos < len && !dead; pos += kTriWarps) {
+      fetch_row<B, UPPER>(nxt, pos + kTriWarps, len, s_i, s_beg, s_end, ci, vals, dinv, rhs, g, rr,
+                          act, lane);
+      const int i = cur.i;
+      double acc = 0.0;
+      bool ok = true;
+      for (int t0 = cur.beg; t0 < cur.end; t0 += G) {
+        const int t = t0 + g;
+        if (act && t < cur.end) {
+          int j;
+          double av[B];
+          if (t0 == cur.beg) {
+            j = cur.j;
+#pragma unroll
+            for (int q = 0; q < B; ++q) av[q] = cur.av[q];
+          } else {
+            j = __ldg(ci + t);
+            const double* a = vals + (size_t)t * (B * B) + rr;
+#pragma unroll
+            for (int q = 0; q < B; ++q) av[q] = __ldg(a + q * B);
+          }
+          double yj[B];
+          if (j >= lo && j < hi) {
+            ok = wait_local_flag(fl + (j - lo), c, w);
+            if (ok) {
+#pragma unroll
+              for (int q = 0; q < B; ++q) yj[q] = yl[(j - lo) * B + q];
+            }
+          } else {
+#pragma unroll
+            for (int q = 0; q < B; ++q)
+              if (ok) ok = wait_value(out + (size_t)j * B + q, yj[q], w);
+          }
+          if (ok) {
+#pragma unroll
+            for (int q = 0; q < B; ++q) acc = fma(av[q], yj[q], acc);
+          }
+        }
+      }
+      if (__any_sync(kFull, !ok)) {
+        dead = true;
+        break;
+      }
+#pragma unroll
+      for (int d = G / 2; d >= 1; d >>= 1) acc += __shfl_down_sync(kFull, acc, d * B);
+      double v = 0.0;
+      if (lane < B) {
+        if (!UPPER) {
+          v = cur.own - acc;
+        } else {
+          double z = 0.0;
+#pragma unroll
+          for (int q = 0; q < B; ++q) z = fma(cur.d[q], cur.yi[q], z);
+          v = z - acc;
+        }
+        if (i != skip_row) publish(out + (size_t)i * B + lane, v);
+        if (!UPPER) reinterpret_cast<unsigned long long*>(pend_out)[(size_t)i * B + lane] = kPending;
+      }
+      // one lane writes the row's B values to shared memory, then releases its flag
+#pragma unroll
+      for (int q = 0; q < B; ++q) {
+        const double vq = __shfl_sync(kFull, v, q);
+        if (lane == 0) yl[(i - lo) * B + q] = vq;
+      }
+      if (lane == 0) st_release_cta_shared_s32(fl + (i - lo), c);
+      cur = nxt;
+    }
+  }
+}
+
+int sm_count() {
+  static int cached = 0;
+  if (!cached) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&cached, cudaDevAttrMultiProcessorCount, dev);
+    if (cached <= 0) cached = 1;
+  }
+  return cached;
+}
+
+size_t tri_smem_bytes(int chunk, int b) { return (size_t)chunk * (b * sizeof(double) + 4 * sizeof(int)); }
+
+// Persistent grid: as many CTAs as fit on the device at once (cached per
+// chunk size; the occupancy query is host work worth skipping per launch).
+template <int B, bool UPPER>
+int tri_grid(int chunk, int nchunks) {
+  static int last_chunk = -1, last_per_sm = 1;
+  if (chunk != last_chunk) {
+    const size_t smem = tri_smem_bytes(chunk, B);
+    cudaFuncSetAttribute(tri_solve_kernel<B, UPPER>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)std::max<size_t>(smem, 48 * 1024));
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tri_solve_kernel<B, UPPER>, kTriWarps * 32, smem);
+    last_per_sm = per_sm < 1 ? 1 : per_sm;
+    last_chunk = chunk;
+  }
+  return std::max(1, std::min(nchunks, last_per_sm * sm_count()));
+}
+
+}  // namespace
+
+int ensure_schedule(bilu_pattern* p, int32_t chunk) {
+  if (p->sched_chunk == chunk && (p->d_sched || p->n == 0)) return 0;
+  build_schedule(p, chunk);
+  if (p->d_sched) {
+    cudaFree(p->d_sched);
+    p->d_sched = nullptr;
+  }
+  if (p->n == 0) return 0;
+  const size_t one = align256(sizeof(int32_t) * (size_t)p->n);
+  void* mem = nullptr;
+  if (cudaMalloc(&mem, 2 * one) != cudaSuccess) {
+    cudaGetLastError();
+    p->sched_chunk = 0;
+    return (int)cudaErrorMemoryAllocation;
+  }
+  p->d_sched = mem;
+  p->d_ord_l = (int32_t*)mem;
+  p->d_ord_u = (int32_t*)((char*)mem + one);
+  cudaMemcpy(p->d_ord_l, p->ord_l.data(), sizeof(int32_t) * p->n, cudaMemcpyHostToDevice);
+  cudaMemcpy(p->d_ord_u, p->ord_u.data(), sizeof(int32_t) * p->n, cudaMemcpyHostToDevice);
+  return (int)cudaGetLastError();
+}
+
+size_t apply_workspace_bytes(int32_t n, int32_t b) {
+  return kHeaderBytes + align256((size_t)n * b * sizeof(double));
+}
+
+int launch_apply(const bilu_pattern* p, int32_t b, const double* f, const double* r, double* x,
+                 void* work, int32_t* stop, void* stream) {
+  const int32_t n = p->n;
+  if (n == 0) return 0;
+  cudaStream_t s = (cudaStream_t)stream;
+  const TrisolveConfig& cfg = trisolve_config();
+  const int chunk = p->sched_chunk;
+  if (chunk <= 0 || !p->d_sched) return (int)cudaErrorInvalidValue;
+  int32_t* header = reinterpret_cast<int32_t*>(work);
+  double* y = reinterpret_cast<double*>(reinterpret_cast<char*>(work) + kHeaderBytes);
+  const size_t bb = (size_t)b * b;
+  const double* L = f;
+  const double* Dinv = f + (size_t)p->nnz_l() * bb;
+  const double* U = Dinv + (size_t)n * bb;
+  const int nchunks = (n + chunk - 1) / chunk;
+  const size_t smem = tri_smem_bytes(chunk, b);
+  const long long m = (long long)n * b;
+  const int prep_blocks = (int)std::min<long long>((m + 255) / 256, (long long)sm_count() * 8);
+  {
+    ProfScope ps(BILU_PROF_APPLY_PREP, stream);
+    apply_prep_kernel<<<prep_blocks, 256, 0, s>>>(y, m, header, stop);
+  }
+  BILU_DISPATCH_B(b, {
+    {
+      const int grid = tri_grid<B, false>(chunk, nchunks);
+      ProfScope ps(BILU_PROF_LOWER, stream);
+      tri_solve_kernel<B, false><<<grid, kTriWarps * 32, smem, s>>>(
+          n, chunk, nchunks, p->d_lrp, p->d_lci, L, nullptr, p->d_ord_l, r, y, x, header, cfg.spin_ns,
+          cfg.skip_row, stop);
+    }
+    {
+      const int grid = tri_grid<B, true>(chunk, nchunks);
+      ProfScope ps(BILU_PROF_UPPER, stream);
+      tri_solve_kernel<B, true><<<grid, kTriWarps * 32, smem, s>>>(
+          n, chunk, nchunks, p->d_urp, p->d_uci, U, Dinv, p->d_ord_u, y, x, nullptr, header,
+          cfg.spin_ns, -1, stop);
+    }
+  });
+  return (int)cudaGetLastError();
+}
+
+}  // namespace bilu

@@ -9,3 +9,14 @@ if ROOT not in sys.path:
 def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA GPU (GB300, sm_103a)")
     config.addinivalue_line("markers", "slow: larger CPU cases")
+
+import pytest
+
+
+@pytest.fixture(scope="session")
+def libbilu():
+    """libbilu.so, built in-tree if absent (nvcc cross-compiles without a GPU)."""
+    from paper_1703_01325_gb300 import _lib, build
+    if not os.path.exists(_lib.LIB_PATH):
+        build.build()
+    return _lib.load()
