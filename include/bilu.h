@@ -191,6 +191,33 @@ int bilu_apply(const bilu_pattern* p, int32_t b, const double* d_factors, const 
  */
 int bilu_workspace_status(const void* d_work, void* stream);
 
+/*
+ * bilu_apply_noalloc -- the same x = M^{-1} r as bilu_apply, for callers that
+ * must not allocate device memory: a host program that owns all device memory
+ * and gives plugins none of it, or code that cannot afford the device-wide
+ * synchronisation a cudaMalloc or cudaFree may cause, so it has no workspace
+ * to pass.  The paper has no counterpart; this is a deployment variant.
+ *   Scratch: a fixed 32 MiB array inside the library (every GPU that loads
+ *   the library holds it until the process exits).  The call allocates
+ *   nothing and calls no allocating routine.
+ *   Limit: n*b*8 + 256 bytes must fit in 32 MiB (n*b <= 4,194,272);
+ *   larger systems return BILU_ERR_STATE without launching anything.
+ *   Set-up: the first call on each device looks up the array's device
+ *   address (with that device current); make that first call before any
+ *   stream capture begins.  The pattern must have been uploaded
+ *   (bilu_pattern_upload builds the solve order this call reuses; a chunk
+ *   size set later with bilu_set_trisolve_chunk is not applied here).
+ *   Sharing: every call uses the same array, whose contents persist between
+ *   calls; each call resets what must start cleared before use.  Calls whose
+ *   work overlaps on the GPU (different streams, other threads) race on the
+ *   array and give wrong results: serialise them.
+ *   Arguments as for bilu_apply, without the workspace.  Asynchronous; a
+ *   bounded dependency wait that runs out (which correct use never causes)
+ *   is not reported by this call.
+ */
+int bilu_apply_noalloc(const bilu_pattern* p, int32_t b, const double* d_factors, const double* d_r,
+                       double* d_x, void* stream);
+
 /* ------------------------------------------------------------------------ */
 /* Block SpMV (device)                                                       */
 /* ------------------------------------------------------------------------ */

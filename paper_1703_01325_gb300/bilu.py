@@ -181,6 +181,17 @@ def bilu_apply(pattern: Pattern, b: int, factors: torch.Tensor, r: torch.Tensor,
     return x
 
 
+def bilu_apply_noalloc(pattern: Pattern, b: int, factors: torch.Tensor, r: torch.Tensor,
+                       x: torch.Tensor, stream=None) -> int:
+    """x = (L D U')^{-1} r using the library's fixed scratch array instead of a
+    workspace (for callers that may not allocate device memory).  The caller
+    still provides x.  Returns the library status (BILU_ERR_STATE when the
+    system is too large for the fixed scratch)."""
+    return L.load().bilu_apply_noalloc(pattern.handle, b, _dev(factors, torch.float64, "factors"),
+                                       _dev(r, torch.float64, "r"), _dev(x, torch.float64, "x"),
+                                       _stream_handle(stream))
+
+
 def bilu_workspace_status(work: torch.Tensor, stream=None) -> int:
     return L.load().bilu_workspace_status(_dev(work, torch.uint8, "work"), _stream_handle(stream))
 
