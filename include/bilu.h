@@ -286,6 +286,56 @@ int bicgstab_solve(const bilu_pattern* p, const bilu_bsr* A, const double* d_fac
                    const double* d_rhs, double* d_x, double tol, int32_t maxit, void* d_work,
                    size_t work_bytes, void* stream, bilu_solve_info* info);
 
+/* ------------------------------------------------------------------------ */
+/* Mixed precision: FP32-stored preconditioner, FP64 refinement             */
+/* ------------------------------------------------------------------------ */
+/*
+ * The paper works in FP64 throughout (Section 3).  These calls keep L, U' and
+ * D^{-1} (and a copy of A for the inner SpMV) in FP32 and apply them in FP32
+ * arithmetic, while every Krylov vector, scalar, dot product and the outer
+ * residual stay FP64.  Layouts are those of the FP64 calls with float in
+ * place of double.
+ */
+
+/* Bytes of an FP32 factor buffer (same three sections as bilu_factor_bytes). */
+size_t bilu_factor_bytes_f32(const bilu_pattern* p, int32_t b);
+
+/* d_dst[q] = (float)d_src[q] for q < count (device; round to nearest).  Makes
+ * the FP32 factor buffer from bilu_factor's output (count = nslots*b*b, i.e.
+ * bilu_factor_bytes / 8) and the FP32 copy of A's values.  Asynchronous. */
+int bilu_convert_f32(const double* d_src, float* d_dst, int64_t count, void* stream);
+
+/* x = M^{-1} r with the FP32 factors (Eq. 6, Algorithm 7; FP32 products and
+ * sums, r read and x written in FP64).  Workspace as for bilu_apply.
+ * Asynchronous; status of the bounded waits via bilu_workspace_status. */
+int bilu_apply_f32(const bilu_pattern* p, int32_t b, const float* d_factors32, const double* d_r,
+                   double* d_x, void* d_work, size_t work_bytes, void* stream);
+
+/* y = A x with A's values in FP32 (FP32 products and sums; x read and y
+ * written in FP64).  Asynchronous. */
+int bsr_spmv_f32(int32_t n, int32_t b, const int32_t* d_row_ptr, const int32_t* d_col_idx,
+                 const float* d_vals32, const double* d_x, double* d_y, void* stream);
+
+/* Scratch bytes bicgstab_solve_mixed needs. */
+size_t bicgstab_mixed_workspace_bytes(const bilu_pattern* p, int32_t b);
+
+/*
+ * bicgstab_solve_mixed -- iterative refinement around FP32-preconditioned
+ * BiCGSTAB:  repeat  r = rhs - A x (FP64 SpMV, A->vals);  stop when
+ * ||r||/||rhs|| <= tol;  solve A d = r by BiCGSTAB (the algorithm of
+ * bicgstab_solve) with the FP32 SpMV (d_vals32) and the FP32 preconditioner
+ * (d_factors32) until its recurrence residual drops by inner_tol or
+ * inner_maxit iterations pass;  x += d.
+ *   tol in (0, 1), inner_tol in (0, 1), maxit >= 0 (total inner iterations),
+ *   inner_maxit >= 1; other arguments as for bicgstab_solve.
+ * info->iters counts inner iterations, info->true_relres is the FP64 residual
+ * of the returned x.  Synchronises the stream between refinement steps.
+ */
+int bicgstab_solve_mixed(const bilu_pattern* p, const bilu_bsr* A, const float* d_vals32,
+                         const float* d_factors32, const double* d_rhs, double* d_x, double tol,
+                         int32_t maxit, double inner_tol, int32_t inner_maxit, void* d_work,
+                         size_t work_bytes, void* stream, bilu_solve_info* info);
+
 #ifdef __cplusplus
 }
 #endif

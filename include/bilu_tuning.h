@@ -16,8 +16,8 @@ extern "C" {
 #endif
 
 /* Consecutive block rows one CTA owns in the sync-free triangular solves
- * (default 1024).  Dependencies inside a chunk resolve through shared memory,
- * dependencies across chunks through global memory.  1 <= rows <= 2048, else
+ * (default 512).  Dependencies inside a chunk resolve through shared memory,
+ * dependencies across chunks through global memory.  1 <= rows <= 1024, else
  * BILU_ERR_ARG.  The per-chunk row order is rebuilt (host work plus one
  * device allocation) by the next apply or solve on each pattern. */
 int bilu_set_trisolve_chunk(int32_t rows);

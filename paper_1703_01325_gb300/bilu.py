@@ -230,6 +230,67 @@ def bicgstab_solve(pattern: Pattern, A, factors: torch.Tensor, rhs: torch.Tensor
     return x, info
 
 
+# ---- mixed precision ----
+
+def bilu_convert_f32(src: torch.Tensor, dst: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """FP32 copy of an FP64 device array (factors or matrix values)."""
+    if dst is None:
+        dst = torch.empty(src.numel(), dtype=torch.float32, device=src.device)
+    _check(L.load().bilu_convert_f32(_dev(src, torch.float64, "src"), _dev(dst, torch.float32, "dst"),
+                                     src.numel(), _stream_handle(stream)), "bilu_convert_f32")
+    return dst
+
+
+def bilu_apply_f32(pattern: Pattern, b: int, factors32: torch.Tensor, r: torch.Tensor,
+                   x: torch.Tensor | None = None, work: torch.Tensor | None = None, stream=None):
+    """x = M^{-1} r with FP32-stored factors (FP32 arithmetic, FP64 vectors)."""
+    if x is None:
+        x = torch.empty_like(r)
+    if work is None:
+        work = workspace(pattern.apply_workspace_bytes(b), r.device)
+    _check(L.load().bilu_apply_f32(pattern.handle, b, _dev(factors32, torch.float32, "factors32"),
+                                   _dev(r, torch.float64, "r"), _dev(x, torch.float64, "x"),
+                                   _dev(work, torch.uint8, "work"), work.numel(), _stream_handle(stream)),
+           "bilu_apply_f32")
+    return x
+
+
+def bsr_spmv_f32(n: int, b: int, row_ptr: torch.Tensor, col_idx: torch.Tensor, vals32: torch.Tensor,
+                 x: torch.Tensor, y: torch.Tensor | None = None, stream=None):
+    """y = A x with A's values in FP32 (FP32 arithmetic, FP64 vectors)."""
+    if y is None:
+        y = torch.empty_like(x)
+    _check(L.load().bsr_spmv_f32(n, b, _dev(row_ptr, torch.int32, "row_ptr"),
+                                 _dev(col_idx, torch.int32, "col_idx"), _dev(vals32, torch.float32, "vals32"),
+                                 _dev(x, torch.float64, "x"), _dev(y, torch.float64, "y"),
+                                 _stream_handle(stream)), "bsr_spmv_f32")
+    return y
+
+
+def bicgstab_solve_mixed(pattern: Pattern, A, vals32: torch.Tensor, factors32: torch.Tensor,
+                         rhs: torch.Tensor, x: torch.Tensor | None = None, tol: float = 1e-8,
+                         maxit: int = 1000, inner_tol: float = 1e-4, inner_maxit: int = 200,
+                         work: torch.Tensor | None = None, stream=None):
+    """FP64 iterative refinement around FP32-preconditioned BiCGSTAB.
+    Returns (x, info) like bicgstab_solve."""
+    n, b, rp, ci, vals = A
+    if x is None:
+        x = torch.zeros_like(rhs)
+    if work is None:
+        work = workspace(int(L.load().bicgstab_mixed_workspace_bytes(pattern.handle, b)), rhs.device)
+    bsr = L.BSR(n, b, _dev(rp, torch.int32, "row_ptr"), _dev(ci, torch.int32, "col_idx"),
+                _dev(vals, torch.float64, "vals"))
+    info = L.SolveInfo()
+    st = L.load().bicgstab_solve_mixed(pattern.handle, C.byref(bsr), _dev(vals32, torch.float32, "vals32"),
+                                       _dev(factors32, torch.float32, "factors32"), _dev(rhs, torch.float64, "rhs"),
+                                       _dev(x, torch.float64, "x"), tol, maxit, inner_tol, inner_maxit,
+                                       _dev(work, torch.uint8, "work"), work.numel(), _stream_handle(stream),
+                                       C.byref(info))
+    if st in (L.BILU_ERR_ARG, L.BILU_ERR_STATE, L.BILU_ERR_CUDA, L.BILU_ERR_OOM):
+        _check(st, "bicgstab_solve_mixed")
+    return x, info
+
+
 # ---- tuning / test hooks ----
 
 def bilu_set_trisolve_chunk(rows: int):

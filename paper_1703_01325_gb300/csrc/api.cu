@@ -222,10 +222,76 @@ extern "C" int bicgstab_solve(const bilu_pattern* p, const bilu_bsr* A, const do
   return run_bicgstab(p, A, d_factors, d_rhs, d_x, tol, maxit, d_work, stream, info, g_check_every);
 }
 
+// ---- mixed precision ----
+
+extern "C" size_t bilu_factor_bytes_f32(const bilu_pattern* p, int32_t b) {
+  if (!p || !valid_b(b)) return 0;
+  return (size_t)p->nslots() * b * b * sizeof(float);
+}
+
+extern "C" int bilu_convert_f32(const double* d_src, float* d_dst, int64_t count, void* stream) {
+  if (count < 0 || (count > 0 && (!d_src || !d_dst))) return BILU_ERR_ARG;
+  return cuda_status(launch_convert_f32(d_src, d_dst, count, stream));
+}
+
+extern "C" int bilu_apply_f32(const bilu_pattern* p, int32_t b, const float* d_factors32, const double* d_r,
+                              double* d_x, void* d_work, size_t work_bytes, void* stream) {
+  if (!p || !valid_b(b)) return BILU_ERR_ARG;
+  int st = ready(p);
+  if (st) return st;
+  if (p->n == 0) return BILU_OK;
+  if (!d_factors32 || !d_r || !d_x || !d_work || (const void*)d_r == (const void*)d_x) return BILU_ERR_ARG;
+  if (work_bytes < apply_workspace_bytes(p->n, b)) return BILU_ERR_STATE;
+  if (ensure_schedule(const_cast<bilu_pattern*>(p), trisolve_config().chunk) != 0) return BILU_ERR_OOM;
+  return cuda_status(launch_apply_f32(p, b, d_factors32, d_r, d_x, d_work, nullptr, stream));
+}
+
+extern "C" int bsr_spmv_f32(int32_t n, int32_t b, const int32_t* d_row_ptr, const int32_t* d_col_idx,
+                            const float* d_vals32, const double* d_x, double* d_y, void* stream) {
+  if (n < 0 || !valid_b(b)) return BILU_ERR_ARG;
+  if (n == 0) return BILU_OK;
+  if (!d_row_ptr || !d_col_idx || !d_vals32 || !d_x || !d_y || (const void*)d_x == (const void*)d_y)
+    return BILU_ERR_ARG;
+  return cuda_status(launch_spmv_f32(n, b, d_row_ptr, d_col_idx, d_vals32, d_x, d_y, stream));
+}
+
+extern "C" size_t bicgstab_mixed_workspace_bytes(const bilu_pattern* p, int32_t b) {
+  if (!p || !valid_b(b)) return 0;
+  return krylov_mixed_workspace_bytes(p->n, b);
+}
+
+extern "C" int bicgstab_solve_mixed(const bilu_pattern* p, const bilu_bsr* A, const float* d_vals32,
+                                    const float* d_factors32, const double* d_rhs, double* d_x, double tol,
+                                    int32_t maxit, double inner_tol, int32_t inner_maxit, void* d_work,
+                                    size_t work_bytes, void* stream, bilu_solve_info* info) {
+  if (info) {
+    info->status = BILU_ERR_ARG;
+    info->iters = 0;
+    info->true_relres = 0.0;
+    info->ms = 0.0;
+  }
+  if (!p || !A || !valid_b(A->b) || A->n != p->n || !(tol > 0.0 && tol < 1.0) ||
+      !(inner_tol > 0.0 && inner_tol < 1.0) || maxit < 0 || inner_maxit < 1)
+    return BILU_ERR_ARG;
+  int st = ready(p);
+  if (st) return st;
+  if (p->n == 0) {
+    if (info) info->status = BILU_OK;
+    return BILU_OK;
+  }
+  if (!A->row_ptr || !A->col_idx || !A->vals || !d_vals32 || !d_factors32 || !d_rhs || !d_x || !d_work ||
+      (const void*)d_rhs == (const void*)d_x)
+    return BILU_ERR_ARG;
+  if (work_bytes < krylov_mixed_workspace_bytes(p->n, A->b)) return BILU_ERR_STATE;
+  if (ensure_schedule(const_cast<bilu_pattern*>(p), trisolve_config().chunk) != 0) return BILU_ERR_OOM;
+  return run_bicgstab_mixed(p, A, d_vals32, d_factors32, d_rhs, d_x, tol, maxit, inner_tol, inner_maxit,
+                            d_work, stream, info, g_check_every);
+}
+
 // ---- tuning and test hooks (include/bilu_tuning.h) ----
 
 extern "C" int bilu_set_trisolve_chunk(int32_t rows) {
-  if (rows < 1 || rows > 2048) return BILU_ERR_ARG;
+  if (rows < 1 || rows > 1024) return BILU_ERR_ARG;
   trisolve_config().chunk = rows;
   return BILU_OK;
 }
@@ -251,7 +317,7 @@ extern "C" int bilu_test_withhold_row(int32_t row) {
 
 extern "C" int bilu_schedule_export(const bilu_pattern* p, int32_t rows, int32_t* ord_lower,
                                     int32_t* ord_upper) {
-  if (!p || rows < 1 || rows > 2048 || (p->n > 0 && (!ord_lower || !ord_upper))) return BILU_ERR_ARG;
+  if (!p || rows < 1 || rows > 1024 || (p->n > 0 && (!ord_lower || !ord_upper))) return BILU_ERR_ARG;
   bilu_pattern tmp;
   tmp.n = p->n;
   tmp.lrp = p->lrp;

@@ -4,6 +4,7 @@
 
 #include <cstddef>
 #include <cstdint>
+#include <functional>
 #include <vector>
 
 #include "../../include/bilu.h"
@@ -66,7 +67,7 @@ constexpr long long kDefaultSpinNs = 2000000000LL;  // 2 s
 
 // Tunables of the sync-free triangular solves (see trisolve.cu).
 struct TrisolveConfig {
-  int chunk = 1024;        // consecutive block rows processed by one CTA
+  int chunk = 512;         // consecutive block rows processed by one CTA
   long long spin_ns = kDefaultSpinNs;
   int skip_row = -1;       // test hook: this row of the lower solve is never published
 };
@@ -89,6 +90,9 @@ class ProfScope {
 // ---- kernels (launchers return cudaError_t as int) ----
 int launch_spmv(int32_t n, int32_t b, const int32_t* rp, const int32_t* ci, const double* vals,
                 const double* x, double* y, void* stream, const int32_t* stop = nullptr);
+int launch_spmv_f32(int32_t n, int32_t b, const int32_t* rp, const int32_t* ci, const float* vals,
+                    const double* x, double* y, void* stream, const int32_t* stop = nullptr);
+int launch_convert_f32(const double* src, float* dst, long long count, void* stream);
 
 int launch_backfill(const bilu_pattern* p, int32_t b, const double* a_vals, double* f, void* stream);
 int launch_factor(const bilu_pattern* p, int32_t b, double* f, int32_t* header, int32_t* done,
@@ -101,8 +105,24 @@ int ensure_schedule(bilu_pattern* p, int32_t chunk);
 void build_schedule(bilu_pattern* p, int32_t chunk);  // host part (symbolic.cpp)
 int launch_apply(const bilu_pattern* p, int32_t b, const double* f, const double* r, double* x,
                  void* work, int32_t* stop, void* stream);
+int launch_apply_f32(const bilu_pattern* p, int32_t b, const float* f, const double* r, double* x,
+                     void* work, int32_t* stop, void* stream);
+
+// The operators a BiCGSTAB run uses: y = A x and z = M^{-1} r, both gated by
+// the device stop word (nullptr: always run); `work` is the apply workspace.
+struct KOps {
+  std::function<int(const double*, double*, int32_t*, void*)> spmv;
+  std::function<int(const double*, double*, int32_t*, void*)> apply;
+};
 
 size_t krylov_workspace_bytes(int32_t n, int32_t b);
+size_t krylov_mixed_workspace_bytes(int32_t n, int32_t b);
+int bicgstab_core(const KOps& ops, long long m, const double* rhs, double* x, double tol, int32_t maxit,
+                  bool confirm, void* work, void* stream, int batch, int32_t* iters_out, double* relres_out,
+                  double* bnorm2_out);
+int run_bicgstab_mixed(const bilu_pattern* p, const bilu_bsr* A, const float* vals32, const float* f32,
+                       const double* rhs, double* x, double tol, int32_t maxit, double inner_tol,
+                       int32_t inner_maxit, void* work, void* stream, bilu_solve_info* info, int batch);
 int run_bicgstab(const bilu_pattern* p, const bilu_bsr* A, const double* f, const double* rhs,
                  double* x, double tol, int32_t maxit, void* work, void* stream,
                  bilu_solve_info* info, int batch);

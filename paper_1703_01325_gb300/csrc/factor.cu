@@ -29,7 +29,6 @@
 namespace bilu {
 namespace {
 
-constexpr int kFactorWarps = 8;
 
 __global__ void backfill_kernel(long long total, int bb, const int32_t* __restrict__ slot_src,
                                 const double* __restrict__ a, double* __restrict__ f) {
@@ -54,6 +53,7 @@ __global__ void factor_init_kernel(int32_t* header, int32_t* done, int32_t n) {
 // memory through the same slot interface.
 template <int B>
 struct FactorCap {
+  static constexpr int W = B <= 5 ? 16 : 8;            // warps per CTA
   static constexpr int RC = B <= 4 ? 64 : (B <= 6 ? 32 : 24);
   static constexpr int WDBL = RC * B * B + 4 * B * B;  // doubles per warp
   static constexpr int WINT = RC + 32;                 // ints per warp
@@ -61,12 +61,12 @@ struct FactorCap {
 
 template <int B>
 size_t factor_smem_bytes(int chunk) {
-  return (size_t)kFactorWarps * FactorCap<B>::WDBL * sizeof(double) +
-         ((size_t)2 * chunk + (size_t)kFactorWarps * FactorCap<B>::WINT) * sizeof(int);
+  return (size_t)FactorCap<B>::W * FactorCap<B>::WDBL * sizeof(double) +
+         ((size_t)2 * chunk + (size_t)FactorCap<B>::W * FactorCap<B>::WINT) * sizeof(int);
 }
 
 template <int B>
-__global__ void __launch_bounds__(kFactorWarps * 32) factor_kernel(
+__global__ void __launch_bounds__(FactorCap<B>::W * 32) factor_kernel(
     int32_t n, int32_t chunk, int32_t nchunks, const int32_t* __restrict__ ord,
     const int32_t* __restrict__ lrp, const int32_t* __restrict__ lci,
     const int32_t* __restrict__ urp, const int32_t* __restrict__ uci, double* f, long long nnz_l,
@@ -81,7 +81,7 @@ __global__ void __launch_bounds__(kFactorWarps * 32) factor_kernel(
   double* dp = rowv + RC * BB;   // D_p^{-1}
   double* aip = dp + BB;         // scaled A_ip
   double* aug = aip + BB;        // [D_i | I] for Gauss-Jordan
-  int* ib = reinterpret_cast<int*>(reinterpret_cast<double*>(smem_raw) + (size_t)kFactorWarps * FactorCap<B>::WDBL);
+  int* ib = reinterpret_cast<int*>(reinterpret_cast<double*>(smem_raw) + (size_t)FactorCap<B>::W * FactorCap<B>::WDBL);
   int* fl = ib;                  // chunk-local ready flags (value = chunk id)
   int* s_i = fl + chunk;         // rows of the chunk in local-level order
   int* cols = s_i + chunk + warp * FactorCap<B>::WINT;  // column of each staged slot
@@ -108,7 +108,7 @@ __global__ void __launch_bounds__(kFactorWarps * 32) factor_kernel(
     const int len = hi - lo;
     for (int q = tid; q < len; q += blockDim.x) s_i[q] = ord[lo + q];
     __syncthreads();
-    for (int pos = warp; pos < len && !dead; pos += kFactorWarps) {
+    for (int pos = warp; pos < len && !dead; pos += FactorCap<B>::W) {
       const int i = s_i[pos];
       const int lb = lrp[i], nl = lrp[i + 1] - lb;
       const int ub = urp[i], nu = urp[i + 1] - ub;
@@ -160,8 +160,24 @@ __global__ void __launch_bounds__(kFactorWarps * 32) factor_kernel(
           dead = true;
           break;
         }
-        // A_ip <- A_ip * D_p^{-1}
+        // A_ip <- A_ip * D_p^{-1}; D_p^{-1} and this lane's first U_pj
+        // operands are fetched together (one memory round trip per pivot)
         for (int e = lane; e < BB; e += 32) dp[e] = D[(size_t)p * BB + e];
+        constexpr int NPRE = 4;
+        double upre[NPRE][B];
+        {
+          const int cnt0 = min(32, pe - pb);
+#pragma unroll
+          for (int h = 0; h < NPRE; ++h) {
+            const int wk = lane + 32 * h;
+            if (wk < cnt0 * BB) {
+              const int sidx = wk / BB, e = wk - (wk / BB) * BB;
+              const double* upj = U + (size_t)(pb + sidx) * BB + (e / B) * B;
+#pragma unroll
+              for (int m = 0; m < B; ++m) upre[h][m] = upj[m];
+            }
+          }
+        }
         __syncwarp();
         double* a = blk(k);
         double nv[H];
@@ -193,7 +209,24 @@ __global__ void __launch_bounds__(kFactorWarps * 32) factor_kernel(
             __syncwarp();
           }
           const int cnt = min(32, pe - s0);
-          for (int wk = lane; wk < cnt * BB; wk += 32) {
+          if (s0 == pb) {
+#pragma unroll
+            for (int h = 0; h < NPRE; ++h) {
+              const int wk = lane + 32 * h;
+              if (wk < cnt * BB) {
+                const int sidx = wk / BB, e = wk - (wk / BB) * BB;
+                const int d = dstv[sidx];
+                if (d >= 0) {
+                  const int r = e % B;
+                  double s = 0.0;
+#pragma unroll
+                  for (int m = 0; m < B; ++m) s = fma(aip[m * B + r], upre[h][m], s);
+                  blk(d)[e] -= s;
+                }
+              }
+            }
+          }
+          for (int wk = lane + (s0 == pb ? 32 * NPRE : 0); wk < cnt * BB; wk += 32) {
             const int sidx = wk / BB;
             const int e = wk - sidx * BB;
             const int d = dstv[sidx];
@@ -355,13 +388,13 @@ int launch_factor(const bilu_pattern* p, int32_t b, double* f, int32_t* header, 
       cudaFuncSetAttribute(factor_kernel<B>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)std::max<size_t>(smem, 48 * 1024));
       int q = 0;
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&q, factor_kernel<B>, kFactorWarps * 32, smem);
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&q, factor_kernel<B>, FactorCap<B>::W * 32, smem);
       per_sm = q < 1 ? 1 : q;
       last_chunk = chunk;
     }
     const int grid = std::max(1, std::min(nchunks, per_sm * sms));
     ProfScope ps(BILU_PROF_FACTOR, stream);
-    factor_kernel<B><<<grid, kFactorWarps * 32, smem, s>>>(n, chunk, nchunks, p->d_ord_l, p->d_lrp, p->d_lci,
+    factor_kernel<B><<<grid, FactorCap<B>::W * 32, smem, s>>>(n, chunk, nchunks, p->d_ord_l, p->d_lrp, p->d_lci,
                                                             p->d_urp, p->d_uci, f, p->nnz_l(), header, done,
                                                             spin);
   });

@@ -20,6 +20,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <functional>
 
 #include "device_common.cuh"
 
@@ -241,6 +242,51 @@ __global__ void k_state_reset(KState* st, int maxit) {
   st->reason = kRunning;
 }
 
+
+// x += d
+__global__ void k_axpy1(long long m, double* x, const double* d) {
+  for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < m;
+       q += (long long)gridDim.x * blockDim.x)
+    x[q] += d[q];
+}
+
+// t = rhs - t; partials (t, t), (rhs, rhs)
+__global__ void k_resid2(long long m, const double* rhs, double* t, double* partials) {
+  double acc[2] = {0.0, 0.0};
+  for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < m;
+       q += (long long)gridDim.x * blockDim.x) {
+    const double b = rhs[q];
+    const double d = b - t[q];
+    t[q] = d;
+    acc[0] = fma(d, d, acc[0]);
+    acc[1] = fma(b, b, acc[1]);
+  }
+  block_reduce_store<2>(acc, partials);
+}
+
+// sums of two partial arrays into out[0..1] (fixed order)
+__global__ void k_sum2(const double* partials, double* out) {
+  __shared__ double tot[2][kRedThreads / 32];
+  double v[2] = {0.0, 0.0};
+  for (int q = 0; q < 2; ++q)
+    for (int k = threadIdx.x; k < kRedBlocks; k += blockDim.x) v[q] += partials[q * kRedBlocks + k];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int q = 0; q < 2; ++q) {
+    for (int d = 16; d >= 1; d >>= 1) v[q] += __shfl_down_sync(kFull, v[q], d);
+    if (lane == 0) tot[q][wid] = v[q];
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0.0, c = 0.0;
+    for (int k = 0; k < kRedThreads / 32; ++k) {
+      a += tot[0][k];
+      c += tot[1][k];
+    }
+    out[0] = a;
+    out[1] = c;
+  }
+}
+
 }  // namespace
 
 size_t krylov_workspace_bytes(int32_t n, int32_t b) {
@@ -249,12 +295,19 @@ size_t krylov_workspace_bytes(int32_t n, int32_t b) {
          apply_workspace_bytes(n, b);
 }
 
-int run_bicgstab(const bilu_pattern* p, const bilu_bsr* A, const double* f, const double* rhs,
-                 double* x, double tol, int32_t maxit, void* work, void* stream,
-                 bilu_solve_info* info, int batch) {
+size_t krylov_mixed_workspace_bytes(int32_t n, int32_t b) {
+  const size_t vec = align256((size_t)n * b * sizeof(double));
+  return krylov_workspace_bytes(n, b) + 2 * vec + 256;
+}
+
+// BiCGSTAB on the operators of `ops`; `x` holds the start vector.  With
+// confirm, convergence is declared only when the recomputed true residual
+// (ops.spmv) confirms it, restarting otherwise; without confirm the loop ends
+// on the recurrence residual (used for the inner solves of the refinement).
+int bicgstab_core(const KOps& ops, long long m, const double* rhs, double* x, double tol, int32_t maxit,
+                  bool confirm, void* work, void* stream, int batch, int32_t* iters_out, double* relres_out,
+                  double* bnorm2_out) {
   cudaStream_t s = (cudaStream_t)stream;
-  const int32_t n = p->n, b = A->b;
-  const long long m = (long long)n * b;
   const size_t vec = align256((size_t)m * sizeof(double));
   char* base = reinterpret_cast<char*>(work);
   KState* st = reinterpret_cast<KState*>(base);
@@ -274,33 +327,27 @@ int run_bicgstab(const bilu_pattern* p, const bilu_bsr* A, const double* f, cons
   int32_t* stop = &st->stop;
   const int vb = kRedBlocks, vt = kRedThreads;
 
-  cudaEvent_t e0, e1;
-  cudaEventCreate(&e0);
-  cudaEventCreate(&e1);
-  cudaEventRecord(e0, s);
   cudaMemsetAsync(aheader, 0, kHeaderBytes, s);
-
   int status = BILU_OK;
   KState hs{};
   { ProfScope ps_(BILU_PROF_KRYLOV, s); k_state_reset<<<1, 1, 0, s>>>(st, maxit); }
   for (;;) {
-    // (re)start from the true residual of the current x
-    int e = launch_spmv(n, b, A->row_ptr, A->col_idx, A->vals, x, t, s);
-    if (e) { status = BILU_ERR_CUDA; break; }
+    // (re)start from the residual of the current x
+    if (ops.spmv(x, t, nullptr, awork)) { status = BILU_ERR_CUDA; break; }
     { ProfScope ps_(BILU_PROF_KRYLOV, s); k_init<<<vb, vt, 0, s>>>(m, rhs, t, r, rh, pv, v, partials); }
     { ProfScope ps_(BILU_PROF_KRYLOV, s); k_fin<<<1, vt, 0, s>>>(st, partials, kFinInit, 2, tol); }
     bool done_loop = false;
     while (!done_loop) {
       for (int it = 0; it < batch; ++it) {
         { ProfScope ps_(BILU_PROF_KRYLOV, s); k_update_p<<<vb, vt, 0, s>>>(m, st, r, pv, v); }
-        launch_apply(p, b, f, pv, ph, awork, stop, s);
-        launch_spmv(n, b, A->row_ptr, A->col_idx, A->vals, ph, v, s, stop);
+        ops.apply(pv, ph, stop, awork);
+        ops.spmv(ph, v, stop, awork);
         { ProfScope ps_(BILU_PROF_KRYLOV, s); k_dot<<<vb, vt, 0, s>>>(m, st, rh, v, partials); }
         { ProfScope ps_(BILU_PROF_KRYLOV, s); k_fin<<<1, vt, 0, s>>>(st, partials, kFinAlpha, 1, tol); }
         { ProfScope ps_(BILU_PROF_KRYLOV, s); k_s<<<vb, vt, 0, s>>>(m, st, r, v, ph, sv, x, partials); }
         { ProfScope ps_(BILU_PROF_KRYLOV, s); k_fin<<<1, vt, 0, s>>>(st, partials, kFinS, 1, tol); }
-        launch_apply(p, b, f, sv, sh, awork, stop, s);
-        launch_spmv(n, b, A->row_ptr, A->col_idx, A->vals, sh, t, s, stop);
+        ops.apply(sv, sh, stop, awork);
+        ops.spmv(sh, t, stop, awork);
         { ProfScope ps_(BILU_PROF_KRYLOV, s); k_dot_ts<<<vb, vt, 0, s>>>(m, st, t, sv, partials); }
         { ProfScope ps_(BILU_PROF_KRYLOV, s); k_fin<<<1, vt, 0, s>>>(st, partials, kFinOmega, 2, tol); }
         { ProfScope ps_(BILU_PROF_KRYLOV, s); k_xr<<<vb, vt, 0, s>>>(m, st, sh, sv, t, rh, x, r, partials); }
@@ -319,19 +366,25 @@ int run_bicgstab(const bilu_pattern* p, const bilu_bsr* A, const double* f, cons
       if (hs.stop) done_loop = true;
     }
     if (status != BILU_OK) break;
+    if (hs.bnorm2 == 0.0) {  // rhs = 0: x = 0 solves it exactly
+      { ProfScope ps_(BILU_PROF_KRYLOV, s); k_zero<<<vb, vt, 0, s>>>(m, x); }
+      hs.true2 = 0.0;
+      status = BILU_OK;
+      break;
+    }
+    if (!confirm) {
+      hs.true2 = hs.last2;
+      status = hs.reason == kConverged ? BILU_OK : hs.reason == kBreakdown ? BILU_ERR_BREAKDOWN
+                                                                           : BILU_ERR_NOT_CONVERGED;
+      break;
+    }
     // true residual
-    launch_spmv(n, b, A->row_ptr, A->col_idx, A->vals, x, t, s);
+    ops.spmv(x, t, nullptr, awork);
     { ProfScope ps_(BILU_PROF_KRYLOV, s); k_resid<<<vb, vt, 0, s>>>(m, rhs, t, partials); }
     { ProfScope ps_(BILU_PROF_KRYLOV, s); k_fin<<<1, vt, 0, s>>>(st, partials, kFinTrue, 1, tol); }
     if (cudaMemcpyAsync(&hs, st, sizeof(KState), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
         cudaStreamSynchronize(s) != cudaSuccess) {
       status = BILU_ERR_CUDA;
-      break;
-    }
-    if (hs.bnorm2 == 0.0) {  // rhs = 0: x = 0 solves it exactly
-      { ProfScope ps_(BILU_PROF_KRYLOV, s); k_zero<<<vb, vt, 0, s>>>(m, x); }
-      hs.true2 = 0.0;
-      status = BILU_OK;
       break;
     }
     const double rel = std::sqrt(hs.true2) / std::sqrt(hs.bnorm2);
@@ -340,16 +393,125 @@ int run_bicgstab(const bilu_pattern* p, const bilu_bsr* A, const double* f, cons
     if (hs.iters >= maxit) { status = BILU_ERR_NOT_CONVERGED; break; }
     // recurrence converged but the true residual did not: restart
   }
-  cudaEventRecord(e1, s);
-  cudaEventSynchronize(e1);
-  float ms = 0.f;
-  cudaEventElapsedTime(&ms, e0, e1);
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
+  if (iters_out) *iters_out = hs.iters;
+  if (relres_out) *relres_out = hs.bnorm2 > 0.0 ? std::sqrt(hs.true2) / std::sqrt(hs.bnorm2) : 0.0;
+  if (bnorm2_out) *bnorm2_out = hs.bnorm2;
+  return status;
+}
+
+namespace {
+
+struct Timer {
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaStream_t s;
+  explicit Timer(cudaStream_t st) : s(st) {
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    cudaEventRecord(e0, s);
+  }
+  double stop_ms() {
+    cudaEventRecord(e1, s);
+    cudaEventSynchronize(e1);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return ms;
+  }
+};
+
+}  // namespace
+
+int run_bicgstab(const bilu_pattern* p, const bilu_bsr* A, const double* f, const double* rhs,
+                 double* x, double tol, int32_t maxit, void* work, void* stream,
+                 bilu_solve_info* info, int batch) {
+  const int32_t n = p->n, b = A->b;
+  KOps ops;
+  ops.spmv = [=](const double* xin, double* yout, int32_t* stop, void*) {
+    return launch_spmv(n, b, A->row_ptr, A->col_idx, A->vals, xin, yout, stream, stop);
+  };
+  ops.apply = [=](const double* rin, double* zout, int32_t* stop, void* aw) {
+    return launch_apply(p, b, f, rin, zout, aw, stop, stream);
+  };
+  Timer timer((cudaStream_t)stream);
+  int32_t iters = 0;
+  double relres = 0.0;
+  const int status = bicgstab_core(ops, (long long)n * b, rhs, x, tol, maxit, true, work, stream, batch, &iters,
+                                   &relres, nullptr);
+  const double ms = timer.stop_ms();
   if (info) {
     info->status = status;
-    info->iters = hs.iters;
-    info->true_relres = hs.bnorm2 > 0.0 ? std::sqrt(hs.true2) / std::sqrt(hs.bnorm2) : 0.0;
+    info->iters = iters;
+    info->true_relres = relres;
+    info->ms = ms;
+  }
+  return status;
+}
+
+// Mixed precision: the outer loop keeps x, the residual and its norm in FP64
+// (r = rhs - A x with the FP64 matrix); each correction d solves A d = r with
+// BiCGSTAB whose SpMV uses the FP32 copy of A and whose preconditioner is the
+// FP32-stored factorization (FP64 Krylov vectors, scalars and dot products),
+// to the relative tolerance inner_tol; then x += d.
+int run_bicgstab_mixed(const bilu_pattern* p, const bilu_bsr* A, const float* vals32, const float* f32,
+                       const double* rhs, double* x, double tol, int32_t maxit, double inner_tol,
+                       int32_t inner_maxit, void* work, void* stream, bilu_solve_info* info, int batch) {
+  cudaStream_t s = (cudaStream_t)stream;
+  const int32_t n = p->n, b = A->b;
+  const long long m = (long long)n * b;
+  const size_t vec = align256((size_t)m * sizeof(double));
+  char* tail = reinterpret_cast<char*>(work) + krylov_workspace_bytes(n, b);
+  double* rout = reinterpret_cast<double*>(tail);
+  double* d = reinterpret_cast<double*>(tail + vec);
+  double* norms = reinterpret_cast<double*>(tail + 2 * vec);  // [(r, r), (rhs, rhs)]
+  double* partials = reinterpret_cast<double*>(reinterpret_cast<char*>(work) + align256(sizeof(KState)));
+  KOps ops;
+  ops.spmv = [=](const double* xin, double* yout, int32_t* stop, void*) {
+    return launch_spmv_f32(n, b, A->row_ptr, A->col_idx, vals32, xin, yout, stream, stop);
+  };
+  ops.apply = [=](const double* rin, double* zout, int32_t* stop, void* aw) {
+    return launch_apply_f32(p, b, f32, rin, zout, aw, stop, stream);
+  };
+  const int vb = kRedBlocks, vt = kRedThreads;
+  Timer timer(s);
+  int status = BILU_ERR_NOT_CONVERGED;
+  int32_t iters = 0;
+  double relres = 0.0;
+  for (int outer = 0;; ++outer) {
+    if (launch_spmv(n, b, A->row_ptr, A->col_idx, A->vals, x, rout, stream, nullptr)) { status = BILU_ERR_CUDA; break; }
+    { ProfScope ps_(BILU_PROF_KRYLOV, s); k_resid2<<<vb, vt, 0, s>>>(m, rhs, rout, partials); }
+    { ProfScope ps_(BILU_PROF_KRYLOV, s); k_sum2<<<1, vt, 0, s>>>(partials, norms); }
+    double hn[2] = {0.0, 0.0};
+    if (cudaMemcpyAsync(hn, norms, sizeof(hn), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess) {
+      status = BILU_ERR_CUDA;
+      break;
+    }
+    if (hn[1] == 0.0) {
+      { ProfScope ps_(BILU_PROF_KRYLOV, s); k_zero<<<vb, vt, 0, s>>>(m, x); }
+      relres = 0.0;
+      status = BILU_OK;
+      break;
+    }
+    relres = std::sqrt(hn[0]) / std::sqrt(hn[1]);
+    if (relres <= tol) { status = BILU_OK; break; }
+    if (iters >= maxit) { status = BILU_ERR_NOT_CONVERGED; break; }
+    cudaMemsetAsync(d, 0, (size_t)m * sizeof(double), s);
+    int32_t it = 0;
+    const int32_t budget = std::min(inner_maxit, maxit - iters);
+    if (budget <= 0) { status = BILU_ERR_NOT_CONVERGED; break; }
+    const int st = bicgstab_core(ops, m, rout, d, inner_tol, budget, false, work, stream, batch, &it, nullptr,
+                                 nullptr);
+    if (st == BILU_ERR_CUDA || st == BILU_ERR_TIMEOUT) { status = st; break; }
+    { ProfScope ps_(BILU_PROF_KRYLOV, s); k_axpy1<<<vb, vt, 0, s>>>(m, x, d); }
+    iters += it;
+    if (st == BILU_ERR_BREAKDOWN && it == 0) { status = BILU_ERR_BREAKDOWN; break; }
+  }
+  const double ms = timer.stop_ms();
+  if (info) {
+    info->status = status;
+    info->iters = iters;
+    info->true_relres = relres;
     info->ms = ms;
   }
   return status;

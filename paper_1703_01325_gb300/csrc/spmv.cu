@@ -10,18 +10,23 @@
 // streamed with cache-streaming loads; x stays in L2 for the gathers.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "device_common.cuh"
 
 namespace bilu {
 namespace {
 
 // Streaming load (cache-streaming: evict-first in L1 and L2).
-__device__ __forceinline__ double ld_stream(const double* p) { return __ldcs(p); }
+template <typename TV>
+__device__ __forceinline__ TV ld_stream(const TV* p) { return __ldcs(p); }
 
-template <int B>
+// TV: the type the matrix is stored in and the products are accumulated in
+// (double, or float for the mixed-precision solver); x and y stay double.
+template <int B, typename TV>
 __global__ void __launch_bounds__(256) spmv_kernel(int32_t n, const int32_t* __restrict__ rp,
                                                    const int32_t* __restrict__ ci,
-                                                   const double* __restrict__ vals,
+                                                   const TV* __restrict__ vals,
                                                    const double* __restrict__ x,
                                                    double* __restrict__ y,
                                                    const int32_t* stop) {
@@ -34,24 +39,29 @@ __global__ void __launch_bounds__(256) spmv_kernel(int32_t n, const int32_t* __r
   const long long row = warp * R + q;
   if (q >= R || row >= n) return;
   const int32_t beg = rp[row], end = rp[row + 1];
-  double acc = 0.0;
+  TV acc = TV(0);
   for (int32_t t = beg; t < end; ++t) {
     const int32_t j = __ldg(ci + t);
-    const double* a = vals + (size_t)t * (B * B) + r;
+    const TV* a = vals + (size_t)t * (B * B) + r;
     const double* xj = x + (size_t)j * B;
-    double av[B];
+    TV av[B];
 #pragma unroll
     for (int c = 0; c < B; ++c) av[c] = ld_stream(a + c * B);
 #pragma unroll
-    for (int c = 0; c < B; ++c) acc = fma(av[c], __ldg(xj + c), acc);
+    for (int c = 0; c < B; ++c) acc = fma(av[c], (TV)__ldg(xj + c), acc);
   }
-  y[row * B + r] = acc;
+  y[row * B + r] = (double)acc;
 }
 
-}  // namespace
+__global__ void convert_kernel(const double* __restrict__ src, float* __restrict__ dst, long long count) {
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < count; q += stride)
+    dst[q] = (float)src[q];
+}
 
-int launch_spmv(int32_t n, int32_t b, const int32_t* rp, const int32_t* ci, const double* vals,
-                const double* x, double* y, void* stream, const int32_t* stop) {
+template <typename TV>
+int launch_spmv_t(int32_t n, int32_t b, const int32_t* rp, const int32_t* ci, const TV* vals, const double* x,
+                  double* y, void* stream, const int32_t* stop) {
   if (n == 0) return 0;
   cudaStream_t s = (cudaStream_t)stream;
   BILU_DISPATCH_B(b, {
@@ -60,8 +70,30 @@ int launch_spmv(int32_t n, int32_t b, const int32_t* rp, const int32_t* ci, cons
     const int tpb = 256;
     const long long blocks = (warps * 32 + tpb - 1) / tpb;
     ProfScope ps(BILU_PROF_SPMV, stream);
-    spmv_kernel<B><<<(unsigned)blocks, tpb, 0, s>>>(n, rp, ci, vals, x, y, stop);
+    spmv_kernel<B, TV><<<(unsigned)blocks, tpb, 0, s>>>(n, rp, ci, vals, x, y, stop);
   });
+  return (int)cudaGetLastError();
+}
+
+}  // namespace
+
+int launch_spmv(int32_t n, int32_t b, const int32_t* rp, const int32_t* ci, const double* vals,
+                const double* x, double* y, void* stream, const int32_t* stop) {
+  return launch_spmv_t<double>(n, b, rp, ci, vals, x, y, stream, stop);
+}
+
+int launch_spmv_f32(int32_t n, int32_t b, const int32_t* rp, const int32_t* ci, const float* vals,
+                    const double* x, double* y, void* stream, const int32_t* stop) {
+  return launch_spmv_t<float>(n, b, rp, ci, vals, x, y, stream, stop);
+}
+
+int launch_convert_f32(const double* src, float* dst, long long count, void* stream) {
+  if (count <= 0) return 0;
+  int dev = 0, sms = 1;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const long long blocks = std::min<long long>((count + 255) / 256, (long long)sms * 16);
+  convert_kernel<<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(src, dst, count);
   return (int)cudaGetLastError();
 }
 

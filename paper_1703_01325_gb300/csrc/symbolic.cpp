@@ -223,6 +223,7 @@ void build_schedule(bilu_pattern* p, int32_t chunk) {
   const int32_t n = p->n;
   p->ord_l.assign((size_t)n, 0);
   p->ord_u.assign((size_t)n, 0);
+
   std::vector<int32_t> loc((size_t)std::max(chunk, 1), 0);
   std::vector<std::pair<int32_t, int32_t>> key;
   const int32_t nchunks = (n + chunk - 1) / chunk;

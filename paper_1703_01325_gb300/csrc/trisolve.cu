@@ -14,13 +14,14 @@
 //    restricted to the chunk); the CTA's warps take rows round-robin in that
 //    order, and a dependency inside the chunk is read from shared memory after
 //    an acquire on the row's shared-memory ready flag (release by the writing
-//    lane): a hop of tens of nanoseconds.  In natural order most dependencies
-//    of a grid row lie within a few grid lines, i.e. inside its chunk;
+//    lane).  In natural order most dependencies of a grid row lie within a
+//    few grid lines, i.e. inside its chunk;
 //  * a dependency outside the chunk is read from global memory, waiting until
 //    it no longer holds the "pending" bit pattern: the value is its own ready
 //    flag (no separate flag, no fence, one L2 round trip);
-//  * the column indices and values of a warp's next row are loaded into
-//    registers before the current row's waits start;
+//  * the column indices and values of a warp's next row, and optimistic
+//    reads of its dependencies outside the chunk, are loaded into registers
+//    before the current row's waits start;
 //  * forward progress: a row only waits on rows of earlier positions in its
 //    chunk or of earlier tickets, all held by running warps; every wait is
 //    bounded and gives up with BILU_ERR_TIMEOUT (never a trap), and no warp
@@ -28,6 +29,10 @@
 // Lane mapping inside a row: lane = g*B + r, r the output component, g one of
 // G groups that take the row's blocks round-robin; each lane does B FMAs per
 // block and a log2(G)-step shuffle tree sums the groups.
+//
+// TV is the type the factors are stored and applied in: double, or float for
+// the mixed-precision solver (vectors stay double; each value read is
+// converted, the arithmetic runs in TV).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -60,24 +65,25 @@ __global__ void apply_prep_kernel(double* y, long long m, int32_t* header, const
 }
 
 // Registers a lane holds for one row: the row, its first block of this lane's
-// group (column and this lane's B values), and what the row's own update
-// needs (r_i for L; D_i^{-1} row and y_i for U').
-template <int B, bool UPPER>
+// group (column, this lane's B values, optimistic dependency values), and what
+// the row's own update needs (r_i for L; D_i^{-1} row and y_i for U').
+template <int B, bool UPPER, typename TV>
 struct RowPre {
   int i, beg, end, j;
-  double av[B];
-  double own;       // L: r_i[lane]
-  double d[B];      // U': D_i^{-1}[lane][q]
-  double yi[B];     // U': y_i[q]
+  TV av[B];
+  unsigned long long yv[B];  // dependency values of a block outside the chunk, read early
+  double own;                // L: r_i[lane]
+  TV d[B];                   // U': D_i^{-1}[lane][q]
+  double yi[B];              // U': y_i[q]
 };
 
-template <int B, bool UPPER>
-__device__ __forceinline__ void fetch_row(RowPre<B, UPPER>& p, int pos, int len, const int* s_i,
+template <int B, bool UPPER, typename TV>
+__device__ __forceinline__ void fetch_row(RowPre<B, UPPER, TV>& p, int pos, int len, const int* s_i,
                                           const int* s_beg, const int* s_end,
-                                          const int32_t* __restrict__ ci,
-                                          const double* __restrict__ vals,
-                                          const double* __restrict__ dinv, const double* rhs,
-                                          int g, int rr, bool act, int lane) {
+                                          const int32_t* __restrict__ ci, const TV* __restrict__ vals,
+                                          const TV* __restrict__ dinv, const double* rhs,
+                                          const double* out, int lo, int hi, int g, int rr, bool act,
+                                          int lane) {
   if (pos >= len) {
     p.i = -1;
     p.beg = p.end = 0;
@@ -90,15 +96,20 @@ __device__ __forceinline__ void fetch_row(RowPre<B, UPPER>& p, int pos, int len,
   p.j = -1;
   if (act && t < p.end) {
     p.j = __ldg(ci + t);
-    const double* a = vals + (size_t)t * (B * B) + rr;
+    const TV* a = vals + (size_t)t * (B * B) + rr;
 #pragma unroll
     for (int q = 0; q < B; ++q) p.av[q] = __ldg(a + q * B);
+    // a dependency outside the chunk is usually final already: read it now
+    // (relaxed); if it still holds the pending pattern it is waited for later
+    const bool remote = p.j < lo || p.j >= hi;
+#pragma unroll
+    for (int q = 0; q < B; ++q) p.yv[q] = remote ? ld_relaxed_u64(out + (size_t)p.j * B + q) : kPending;
   }
   if (lane < B) {
     if (!UPPER) {
       p.own = rhs[(size_t)p.i * B + lane];
     } else {
-      const double* di = dinv + (size_t)p.i * (B * B) + lane;
+      const TV* di = dinv + (size_t)p.i * (B * B) + lane;
 #pragma unroll
       for (int q = 0; q < B; ++q) {
         p.d[q] = __ldg(di + q * B);
@@ -108,13 +119,12 @@ __device__ __forceinline__ void fetch_row(RowPre<B, UPPER>& p, int pos, int len,
   }
 }
 
-template <int B, bool UPPER>
+template <int B, bool UPPER, typename TV>
 __global__ void __launch_bounds__(kTriWarps * 32) tri_solve_kernel(
     int32_t n, int32_t chunk, int32_t nchunks, const int32_t* __restrict__ rp,
-    const int32_t* __restrict__ ci, const double* __restrict__ vals,
-    const double* __restrict__ dinv, const int32_t* __restrict__ ord, const double* rhs,
-    double* out, double* pend_out, int32_t* header, long long spin_ns, int32_t skip_row,
-    int32_t* stop) {
+    const int32_t* __restrict__ ci, const TV* __restrict__ vals, const TV* __restrict__ dinv,
+    const int32_t* __restrict__ ord, const double* rhs, double* out, double* pend_out,
+    int32_t* header, long long spin_ns, int32_t skip_row, int32_t* stop) {
   constexpr int G = groups_for(B);
   extern __shared__ __align__(16) unsigned char smem_raw[];
   double* yl = reinterpret_cast<double*>(smem_raw);
@@ -157,28 +167,36 @@ __global__ void __launch_bounds__(kTriWarps * 32) tri_solve_kernel(
       s_end[q] = rp[i + 1];
     }
     __syncthreads();
-    RowPre<B, UPPER> cur, nxt;
-    fetch_row<B, UPPER>(cur, warp, len, s_i, s_beg, s_end, ci, vals, dinv, rhs, g, rr, act, lane);
+    RowPre<B, UPPER, TV> cur, nxt;
+    fetch_row<B, UPPER, TV>(cur, warp, len, s_i, s_beg, s_end, ci, vals, dinv, rhs, out, lo, hi, g, rr, act,
+                            lane);
     for (int pos = warp; pos < len && !dead; pos += kTriWarps) {
-      fetch_row<B, UPPER>(nxt, pos + kTriWarps, len, s_i, s_beg, s_end, ci, vals, dinv, rhs, g, rr,
-                          act, lane);
+      fetch_row<B, UPPER, TV>(nxt, pos + kTriWarps, len, s_i, s_beg, s_end, ci, vals, dinv, rhs, out, lo, hi,
+                              g, rr, act, lane);
       const int i = cur.i;
-      double acc = 0.0;
+      TV acc = TV(0);
       bool ok = true;
       for (int t0 = cur.beg; t0 < cur.end; t0 += G) {
         const int t = t0 + g;
         if (act && t < cur.end) {
           int j;
-          double av[B];
+          TV av[B];
+          unsigned long long yv[B];
           if (t0 == cur.beg) {
             j = cur.j;
 #pragma unroll
-            for (int q = 0; q < B; ++q) av[q] = cur.av[q];
+            for (int q = 0; q < B; ++q) {
+              av[q] = cur.av[q];
+              yv[q] = cur.yv[q];
+            }
           } else {
             j = __ldg(ci + t);
-            const double* a = vals + (size_t)t * (B * B) + rr;
+            const TV* a = vals + (size_t)t * (B * B) + rr;
 #pragma unroll
-            for (int q = 0; q < B; ++q) av[q] = __ldg(a + q * B);
+            for (int q = 0; q < B; ++q) {
+              av[q] = __ldg(a + q * B);
+              yv[q] = kPending;
+            }
           }
           double yj[B];
           if (j >= lo && j < hi) {
@@ -189,12 +207,14 @@ __global__ void __launch_bounds__(kTriWarps * 32) tri_solve_kernel(
             }
           } else {
 #pragma unroll
-            for (int q = 0; q < B; ++q)
-              if (ok) ok = wait_value(out + (size_t)j * B + q, yj[q], w);
+            for (int q = 0; q < B; ++q) {
+              if (yv[q] != kPending) yj[q] = __longlong_as_double((long long)yv[q]);
+              else if (ok) ok = wait_value(out + (size_t)j * B + q, yj[q], w);
+            }
           }
           if (ok) {
 #pragma unroll
-            for (int q = 0; q < B; ++q) acc = fma(av[q], yj[q], acc);
+            for (int q = 0; q < B; ++q) acc = fma(av[q], (TV)yj[q], acc);
           }
         }
       }
@@ -207,12 +227,12 @@ __global__ void __launch_bounds__(kTriWarps * 32) tri_solve_kernel(
       double v = 0.0;
       if (lane < B) {
         if (!UPPER) {
-          v = cur.own - acc;
+          v = (double)((TV)cur.own - acc);
         } else {
-          double z = 0.0;
+          TV z = TV(0);
 #pragma unroll
-          for (int q = 0; q < B; ++q) z = fma(cur.d[q], cur.yi[q], z);
-          v = z - acc;
+          for (int q = 0; q < B; ++q) z = fma(cur.d[q], (TV)cur.yi[q], z);
+          v = (double)(z - acc);
         }
         if (i != skip_row) publish(out + (size_t)i * B + lane, v);
         if (!UPPER) reinterpret_cast<unsigned long long*>(pend_out)[(size_t)i * B + lane] = kPending;
@@ -244,19 +264,61 @@ size_t tri_smem_bytes(int chunk, int b) { return (size_t)chunk * (b * sizeof(dou
 
 // Persistent grid: as many CTAs as fit on the device at once (cached per
 // chunk size; the occupancy query is host work worth skipping per launch).
-template <int B, bool UPPER>
+template <int B, bool UPPER, typename TV>
 int tri_grid(int chunk, int nchunks) {
   static int last_chunk = -1, last_per_sm = 1;
   if (chunk != last_chunk) {
     const size_t smem = tri_smem_bytes(chunk, B);
-    cudaFuncSetAttribute(tri_solve_kernel<B, UPPER>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaFuncSetAttribute(tri_solve_kernel<B, UPPER, TV>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)std::max<size_t>(smem, 48 * 1024));
     int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tri_solve_kernel<B, UPPER>, kTriWarps * 32, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tri_solve_kernel<B, UPPER, TV>, kTriWarps * 32, smem);
     last_per_sm = per_sm < 1 ? 1 : per_sm;
     last_chunk = chunk;
   }
   return std::max(1, std::min(nchunks, last_per_sm * sm_count()));
+}
+
+template <typename TV>
+int launch_apply_t(const bilu_pattern* p, int32_t b, const TV* f, const double* r, double* x, void* work,
+                   int32_t* stop, void* stream) {
+  const int32_t n = p->n;
+  if (n == 0) return 0;
+  cudaStream_t s = (cudaStream_t)stream;
+  const TrisolveConfig& cfg = trisolve_config();
+  const int chunk = p->sched_chunk;
+  if (chunk <= 0 || !p->d_sched) return (int)cudaErrorInvalidValue;
+  int32_t* header = reinterpret_cast<int32_t*>(work);
+  double* y = reinterpret_cast<double*>(reinterpret_cast<char*>(work) + kHeaderBytes);
+  const size_t bb = (size_t)b * b;
+  const TV* L = f;
+  const TV* Dinv = f + (size_t)p->nnz_l() * bb;
+  const TV* U = Dinv + (size_t)n * bb;
+  const int nchunks = (n + chunk - 1) / chunk;
+  const size_t smem = tri_smem_bytes(chunk, b);
+  const long long m = (long long)n * b;
+  const int prep_blocks = (int)std::min<long long>((m + 255) / 256, (long long)sm_count() * 8);
+  {
+    ProfScope ps(BILU_PROF_APPLY_PREP, stream);
+    apply_prep_kernel<<<prep_blocks, 256, 0, s>>>(y, m, header, stop);
+  }
+  BILU_DISPATCH_B(b, {
+    {
+      const int grid = tri_grid<B, false, TV>(chunk, nchunks);
+      ProfScope ps(BILU_PROF_LOWER, stream);
+      tri_solve_kernel<B, false, TV><<<grid, kTriWarps * 32, smem, s>>>(
+          n, chunk, nchunks, p->d_lrp, p->d_lci, L, nullptr, p->d_ord_l, r, y, x, header, cfg.spin_ns,
+          cfg.skip_row, stop);
+    }
+    {
+      const int grid = tri_grid<B, true, TV>(chunk, nchunks);
+      ProfScope ps(BILU_PROF_UPPER, stream);
+      tri_solve_kernel<B, true, TV><<<grid, kTriWarps * 32, smem, s>>>(
+          n, chunk, nchunks, p->d_urp, p->d_uci, U, Dinv, p->d_ord_u, y, x, nullptr, header, cfg.spin_ns, -1,
+          stop);
+    }
+  });
+  return (int)cudaGetLastError();
 }
 
 }  // namespace
@@ -290,43 +352,12 @@ size_t apply_workspace_bytes(int32_t n, int32_t b) {
 
 int launch_apply(const bilu_pattern* p, int32_t b, const double* f, const double* r, double* x,
                  void* work, int32_t* stop, void* stream) {
-  const int32_t n = p->n;
-  if (n == 0) return 0;
-  cudaStream_t s = (cudaStream_t)stream;
-  const TrisolveConfig& cfg = trisolve_config();
-  const int chunk = p->sched_chunk;
-  if (chunk <= 0 || !p->d_sched) return (int)cudaErrorInvalidValue;
-  int32_t* header = reinterpret_cast<int32_t*>(work);
-  double* y = reinterpret_cast<double*>(reinterpret_cast<char*>(work) + kHeaderBytes);
-  const size_t bb = (size_t)b * b;
-  const double* L = f;
-  const double* Dinv = f + (size_t)p->nnz_l() * bb;
-  const double* U = Dinv + (size_t)n * bb;
-  const int nchunks = (n + chunk - 1) / chunk;
-  const size_t smem = tri_smem_bytes(chunk, b);
-  const long long m = (long long)n * b;
-  const int prep_blocks = (int)std::min<long long>((m + 255) / 256, (long long)sm_count() * 8);
-  {
-    ProfScope ps(BILU_PROF_APPLY_PREP, stream);
-    apply_prep_kernel<<<prep_blocks, 256, 0, s>>>(y, m, header, stop);
-  }
-  BILU_DISPATCH_B(b, {
-    {
-      const int grid = tri_grid<B, false>(chunk, nchunks);
-      ProfScope ps(BILU_PROF_LOWER, stream);
-      tri_solve_kernel<B, false><<<grid, kTriWarps * 32, smem, s>>>(
-          n, chunk, nchunks, p->d_lrp, p->d_lci, L, nullptr, p->d_ord_l, r, y, x, header, cfg.spin_ns,
-          cfg.skip_row, stop);
-    }
-    {
-      const int grid = tri_grid<B, true>(chunk, nchunks);
-      ProfScope ps(BILU_PROF_UPPER, stream);
-      tri_solve_kernel<B, true><<<grid, kTriWarps * 32, smem, s>>>(
-          n, chunk, nchunks, p->d_urp, p->d_uci, U, Dinv, p->d_ord_u, y, x, nullptr, header,
-          cfg.spin_ns, -1, stop);
-    }
-  });
-  return (int)cudaGetLastError();
+  return launch_apply_t<double>(p, b, f, r, x, work, stop, stream);
+}
+
+int launch_apply_f32(const bilu_pattern* p, int32_t b, const float* f, const double* r, double* x,
+                     void* work, int32_t* stop, void* stream) {
+  return launch_apply_t<float>(p, b, f, r, x, work, stop, stream);
 }
 
 }  // namespace bilu

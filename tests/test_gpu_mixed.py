@@ -1,0 +1,113 @@
+"""GPU parity of the mixed-precision calls (FP32-stored preconditioner and
+SpMV, FP64 refinement) against the CPU oracle.
+
+The FP32 kernels are compared with the oracle run on the same FP32-rounded
+values (rounding done here with numpy), so what remains is FP32 arithmetic:
+tolerances follow the standard bound |fl(sum) - sum| <= gamma_m sum|terms|
+with gamma_m = m u / (1 - m u), u = 2^-24, m = terms in the sum."""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle  # noqa: E402
+from paper_1703_01325_gb300.reservoir import reservoir_system  # noqa: E402
+from tests.gpu_util import OracleRun, device_system, rel_maxerr  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+DEV = "cuda:0"
+U32 = 2.0 ** -24
+
+
+def gamma(m):
+    return m * U32 / (1 - m * U32)
+
+
+@pytest.fixture(scope="module")
+def B(libbilu):
+    import paper_1703_01325_gb300.bilu as B
+    torch.cuda.set_device(0)
+    return B
+
+
+@pytest.mark.parametrize("b", [1, 2, 3, 5, 8])
+def test_spmv_f32(B, b):
+    S = reservoir_system(11, 7, 5, b, stencil=27, seed=b)
+    rp, ci, vals, _ = device_system(S, DEV)
+    vals32 = B.bilu_convert_f32(vals)
+    x = np.linspace(-1.0, 1.0, S.n * b)
+    y = B.bsr_spmv_f32(S.n, b, rp, ci, vals32, torch.from_numpy(x).to(DEV)).cpu().numpy()
+    v32 = S.vals.astype(np.float32).astype(np.float64)
+    x32 = x.astype(np.float32).astype(np.float64)
+    yo = oracle.spmv(S.n, b, S.row_ptr, S.col_idx, v32, x32)
+    absy = oracle.spmv(S.n, b, S.row_ptr, S.col_idx, np.abs(v32), np.abs(x32))
+    terms = 27 * b
+    assert np.all(np.abs(y - yo) <= 2 * gamma(terms) * absy + 1e-300)
+
+
+def test_convert_f32_rounds_to_nearest(B):
+    x = np.array([1.0, 1.0 + 2.0 ** -30, np.pi, -1e-40, 3.4e38, 1e300, np.nan], np.float64)
+    got = B.bilu_convert_f32(torch.from_numpy(x).to(DEV)).cpu().numpy()
+    ref = x.astype(np.float32)
+    assert np.array_equal(got[:-1], ref[:-1]) and np.isnan(got[-1])
+
+
+@pytest.mark.parametrize("b,k", [(3, 0), (3, 1), (4, 2), (8, 1)])
+def test_apply_f32_matches_rounded_factors(B, b, k):
+    S = reservoir_system(12, 9, 7, b, sigma=1.0, accum=0.01, seed=3 * b + k)
+    o = OracleRun(S.n, b, S.row_ptr, S.col_idx, S.vals, k)
+    rp, ci, vals, rhs = device_system(S, DEV)
+    P = B.bilu_symbolic(S.n, S.row_ptr, S.col_idx, k).upload()
+    F, _ = B.bilu_factor(P, b, vals)
+    F32 = B.bilu_convert_f32(F)
+    x = B.bilu_apply_f32(P, b, F32, rhs).cpu().numpy()
+    # the oracle on the FP32-rounded factors and right-hand side
+    F_r = o.F.astype(np.float32).astype(np.float64)
+    D_r = o.Dinv.astype(np.float32).astype(np.float64)
+    r_r = S.rhs.astype(np.float32).astype(np.float64)
+    xo = oracle.apply(S.n, b, o.prp, o.pci, F_r, D_r, r_r)
+    # FP32 arithmetic through two triangular sweeps: relative error a few
+    # hundred units of u for these well-conditioned factors
+    assert rel_maxerr(x, xo) <= 1e-4
+    # and the FP32 preconditioner is close to the FP64 one
+    assert rel_maxerr(x, o.apply(S.rhs)) <= 1e-3
+
+
+@pytest.mark.parametrize("k", [0, 1])
+def test_bicgstab_mixed_reaches_fp64_accuracy(B, k):
+    S = reservoir_system(16, 16, 8, 3, sigma=1.0, accum=0.01)
+    o = OracleRun(S.n, 3, S.row_ptr, S.col_idx, S.vals, k)
+    rp, ci, vals, rhs = device_system(S, DEV)
+    P = B.bilu_symbolic(S.n, S.row_ptr, S.col_idx, k).upload()
+    F, _ = B.bilu_factor(P, 3, vals)
+    F32 = B.bilu_convert_f32(F)
+    vals32 = B.bilu_convert_f32(vals)
+    A = (S.n, 3, rp, ci, vals)
+    x, info = B.bicgstab_solve_mixed(P, A, vals32, F32, rhs, tol=1e-10, maxit=2000, inner_tol=1e-4,
+                                     inner_maxit=200)
+    assert info.status == 0 and info.true_relres <= 1e-10
+    xg = x.cpu().numpy()
+    res = np.linalg.norm(S.rhs - o.spmv(xg)) / np.linalg.norm(S.rhs)
+    assert res <= 1e-10 * (1 + 1e-6)
+    assert res == pytest.approx(info.true_relres, rel=1e-5, abs=1e-16)
+    xo, _, _, st = oracle.bicgstab(S.n, 3, S.row_ptr, S.col_idx, S.vals, o.prp, o.pci, o.F, o.Dinv, S.rhs,
+                                   tol=1e-12, maxit=2000)
+    assert st == 0
+    assert np.linalg.norm(xg - xo) <= 1e-7 * np.linalg.norm(xo)
+
+
+def test_bicgstab_mixed_edge_cases(B):
+    S = reservoir_system(6, 5, 4, 3, sigma=1.0, accum=0.01)
+    rp, ci, vals, rhs = device_system(S, DEV)
+    P = B.bilu_symbolic(S.n, S.row_ptr, S.col_idx, 0).upload()
+    F, _ = B.bilu_factor(P, 3, vals)
+    F32, vals32 = B.bilu_convert_f32(F), B.bilu_convert_f32(vals)
+    A = (S.n, 3, rp, ci, vals)
+    x, info = B.bicgstab_solve_mixed(P, A, vals32, F32, torch.zeros_like(rhs), x=torch.ones_like(rhs))
+    assert info.status == 0 and info.iters == 0 and not x.any()
+    x, info = B.bicgstab_solve_mixed(P, A, vals32, F32, rhs, tol=1e-14, maxit=3, inner_maxit=2)
+    assert info.status == 5 and info.iters == 3
+    with pytest.raises(B.BiluError):
+        B.bicgstab_solve_mixed(P, A, vals32, F32, rhs, inner_tol=1.5)

@@ -125,7 +125,7 @@ def test_long_chain_b1(B):
     vals = np.where(ci == rows, 4.0, -1.0)[:, None] + 0.1 * random_block_values(len(ci), 1, seed=3)
     rhs = random_block_values(n, 1, seed=4)[:, 0].copy()
     S = BlockSystem(n=n, b=1, row_ptr=rp, col_idx=ci, vals=vals, rhs=rhs)
-    _check_factor_apply(B, S, 0, chunks=(1, 32, 1000, 2048))
+    _check_factor_apply(B, S, 0, chunks=(1, 32, 1000, 1024))
 
 
 def test_single_row_and_block_diagonal(B):
