@@ -300,6 +300,13 @@ int bicgstab_solve(const bilu_pattern* p, const bilu_bsr* A, const double* d_fac
 /* Bytes of an FP32 factor buffer (same three sections as bilu_factor_bytes). */
 size_t bilu_factor_bytes_f32(const bilu_pattern* p, int32_t b);
 
+/* bilu_factor with every step in FP32: A's FP64 values are rounded to FP32
+ * as they are backfilled, and Algorithm 4, the D^{-1} inversion and Eq. 5 run
+ * in FP32 arithmetic into an FP32 factor buffer of bilu_factor_bytes_f32
+ * bytes.  Same workspace, status and info as bilu_factor. */
+int bilu_factor_f32(const bilu_pattern* p, int32_t b, const double* d_a_vals, float* d_factors32,
+                    void* d_work, size_t work_bytes, void* stream, bilu_factor_info* info);
+
 /* d_dst[q] = (float)d_src[q] for q < count (device; round to nearest).  Makes
  * the FP32 factor buffer from bilu_factor's output (count = nslots*b*b, i.e.
  * bilu_factor_bytes / 8) and the FP32 copy of A's values.  Asynchronous. */

@@ -16,12 +16,17 @@ extern "C" {
 #endif
 
 /* Consecutive block rows one CTA owns in the sync-free triangular solves
- * (default 512).  Dependencies inside a chunk resolve through shared memory,
+ * (default 256).  Dependencies inside a chunk resolve through shared memory,
  * dependencies across chunks through global memory.  1 <= rows <= 1024, else
  * BILU_ERR_ARG.  The per-chunk row order is rebuilt (host work plus one
  * device allocation) by the next apply or solve on each pattern. */
 int bilu_set_trisolve_chunk(int32_t rows);
 int32_t bilu_get_trisolve_chunk(void);
+
+/* Warps per CTA in the triangular solves: 4 (default), 8 or 16, else
+ * BILU_ERR_ARG.  More warps per chunk give each row more time to fetch its
+ * operands ahead of its dependencies. */
+int bilu_set_trisolve_warps(int32_t warps);
 
 /* Host copy of the chunk-local row order the sync-free solves use for `rows`
  * rows per chunk (the same order bilu_apply builds): chunk c occupies

@@ -65,6 +65,7 @@ SIGNATURES = {
     "bicgstab_solve": (C.c_int, [_vp, C.POINTER(BSR), _vp, _vp, _vp, C.c_double, C.c_int32, _vp,
                                  C.c_size_t, _vp, C.POINTER(SolveInfo)]),
     "bilu_factor_bytes_f32": (C.c_size_t, [_vp, C.c_int32]),
+    "bilu_factor_f32": (C.c_int, [_vp, C.c_int32, _vp, _vp, _vp, C.c_size_t, _vp, C.POINTER(FactorInfo)]),
     "bilu_convert_f32": (C.c_int, [_vp, _vp, C.c_int64, _vp]),
     "bilu_apply_f32": (C.c_int, [_vp, C.c_int32, _vp, _vp, _vp, _vp, C.c_size_t, _vp]),
     "bsr_spmv_f32": (C.c_int, [C.c_int32, C.c_int32, _vp, _vp, _vp, _vp, _vp, _vp]),
@@ -73,6 +74,7 @@ SIGNATURES = {
                                        C.c_double, C.c_int32, _vp, C.c_size_t, _vp, C.POINTER(SolveInfo)]),
     "bilu_set_trisolve_chunk": (C.c_int, [C.c_int32]),
     "bilu_get_trisolve_chunk": (C.c_int32, []),
+    "bilu_set_trisolve_warps": (C.c_int, [C.c_int32]),
     "bilu_set_spin_limit_ns": (C.c_int, [C.c_int64]),
     "bilu_set_check_every": (C.c_int, [C.c_int32]),
     "bilu_test_withhold_row": (C.c_int, [C.c_int32]),

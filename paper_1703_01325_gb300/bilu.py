@@ -241,6 +241,23 @@ def bilu_convert_f32(src: torch.Tensor, dst: torch.Tensor | None = None, stream=
     return dst
 
 
+def bilu_factor_f32(pattern: Pattern, b: int, a_vals: torch.Tensor, factors32: torch.Tensor | None = None,
+                    work: torch.Tensor | None = None, stream=None, check: bool = True):
+    """The factorization computed and stored in FP32 (from FP64 A values)."""
+    if factors32 is None:
+        nb = int(L.load().bilu_factor_bytes_f32(pattern.handle, b))
+        factors32 = torch.empty(max(nb // 4, 1), dtype=torch.float32, device=a_vals.device)
+    if work is None:
+        work = workspace(pattern.factor_workspace_bytes(b), a_vals.device)
+    info = L.FactorInfo()
+    st = L.load().bilu_factor_f32(pattern.handle, b, _dev(a_vals, torch.float64, "a_vals"),
+                                  _dev(factors32, torch.float32, "factors32"), _dev(work, torch.uint8, "work"),
+                                  work.numel(), _stream_handle(stream), C.byref(info))
+    if check:
+        _check(st, "bilu_factor_f32", f" (bad_row {info.bad_row})" if st == L.BILU_ERR_SINGULAR else "")
+    return factors32, info
+
+
 def bilu_apply_f32(pattern: Pattern, b: int, factors32: torch.Tensor, r: torch.Tensor,
                    x: torch.Tensor | None = None, work: torch.Tensor | None = None, stream=None):
     """x = M^{-1} r with FP32-stored factors (FP32 arithmetic, FP64 vectors)."""
@@ -295,6 +312,10 @@ def bicgstab_solve_mixed(pattern: Pattern, A, vals32: torch.Tensor, factors32: t
 
 def bilu_set_trisolve_chunk(rows: int):
     _check(L.load().bilu_set_trisolve_chunk(rows), "bilu_set_trisolve_chunk")
+
+
+def bilu_set_trisolve_warps(warps: int):
+    _check(L.load().bilu_set_trisolve_warps(warps), "bilu_set_trisolve_warps")
 
 
 def bilu_get_trisolve_chunk() -> int:

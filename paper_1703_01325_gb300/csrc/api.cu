@@ -110,9 +110,11 @@ extern "C" size_t bilu_factor_workspace_bytes(const bilu_pattern* p, int32_t b) 
   return kHeaderBytes + align256(sizeof(int32_t) * ((size_t)p->n + 1));
 }
 
-extern "C" int bilu_factor(const bilu_pattern* p, int32_t b, const double* d_a_vals,
-                           double* d_factors, void* d_work, size_t work_bytes, void* stream,
-                           bilu_factor_info* info) {
+namespace {
+
+template <typename TV>
+int factor_impl(const bilu_pattern* p, int32_t b, const double* d_a_vals, TV* d_factors, void* d_work,
+                size_t work_bytes, void* stream, bilu_factor_info* info) {
   if (info) {
     info->status = BILU_ERR_ARG;
     info->bad_row = -1;
@@ -132,9 +134,15 @@ extern "C" int bilu_factor(const bilu_pattern* p, int32_t b, const double* d_a_v
   cudaEventCreate(&e1);
   cudaEventRecord(e0, s);
   int e = 0;
-  if (p->n > 0) e = launch_backfill(p, b, d_a_vals, d_factors, s);
-  if (!e) e = launch_factor(p, b, d_factors, header, done, s);
-  if (!e) e = launch_scale_upper(p, b, d_factors, s);
+  if constexpr (sizeof(TV) == sizeof(double)) {
+    if (p->n > 0) e = launch_backfill(p, b, d_a_vals, d_factors, s);
+    if (!e) e = launch_factor(p, b, d_factors, header, done, s);
+    if (!e) e = launch_scale_upper(p, b, d_factors, s);
+  } else {
+    if (p->n > 0) e = launch_backfill_f32(p, b, d_a_vals, d_factors, s);
+    if (!e) e = launch_factor_f32(p, b, d_factors, header, done, s);
+    if (!e) e = launch_scale_upper_f32(p, b, d_factors, s);
+  }
   cudaEventRecord(e1, s);
   int32_t hdr[kHeaderWords] = {0};
   if (!e) e = (int)cudaMemcpyAsync(hdr, header, kHeaderBytes, cudaMemcpyDeviceToHost, s);
@@ -151,6 +159,18 @@ extern "C" int bilu_factor(const bilu_pattern* p, int32_t b, const double* d_a_v
     info->ms = ms;
   }
   return st;
+}
+
+}  // namespace
+
+extern "C" int bilu_factor(const bilu_pattern* p, int32_t b, const double* d_a_vals, double* d_factors,
+                           void* d_work, size_t work_bytes, void* stream, bilu_factor_info* info) {
+  return factor_impl<double>(p, b, d_a_vals, d_factors, d_work, work_bytes, stream, info);
+}
+
+extern "C" int bilu_factor_f32(const bilu_pattern* p, int32_t b, const double* d_a_vals, float* d_factors32,
+                               void* d_work, size_t work_bytes, void* stream, bilu_factor_info* info) {
+  return factor_impl<float>(p, b, d_a_vals, d_factors32, d_work, work_bytes, stream, info);
 }
 
 extern "C" size_t bilu_apply_workspace_bytes(const bilu_pattern* p, int32_t b) {
@@ -297,6 +317,12 @@ extern "C" int bilu_set_trisolve_chunk(int32_t rows) {
 }
 
 extern "C" int32_t bilu_get_trisolve_chunk(void) { return trisolve_config().chunk; }
+
+extern "C" int bilu_set_trisolve_warps(int32_t warps) {
+  if (warps != 4 && warps != 8 && warps != 16) return BILU_ERR_ARG;
+  trisolve_config().warps = warps;
+  return BILU_OK;
+}
 
 extern "C" int bilu_set_spin_limit_ns(int64_t ns) {
   if (ns < 1000) return BILU_ERR_ARG;

@@ -27,11 +27,15 @@ struct bilu_pattern {
   // Sync-free solve schedule (see trisolve.cu): rows cut into chunks of
   // sched_chunk consecutive rows (ascending chunks for L, descending for U');
   // ord_l / ord_u list each chunk's rows by local dependency level.
+  // tick_l / tick_u: the chunk each ticket hands out, ordered by the chunk's
+  // level in the chunk dependency graph (then chunk index).
   int32_t sched_chunk = 0;
-  std::vector<int32_t> ord_l, ord_u;
+  std::vector<int32_t> ord_l, ord_u, tick_l, tick_u;
   void* d_sched = nullptr;
   int32_t* d_ord_l = nullptr;
   int32_t* d_ord_u = nullptr;
+  int32_t* d_tick_l = nullptr;
+  int32_t* d_tick_u = nullptr;
   // Device copy (bilu_pattern_upload).
   int device = -1;
   void* d_mem = nullptr;
@@ -67,7 +71,8 @@ constexpr long long kDefaultSpinNs = 2000000000LL;  // 2 s
 
 // Tunables of the sync-free triangular solves (see trisolve.cu).
 struct TrisolveConfig {
-  int chunk = 512;         // consecutive block rows processed by one CTA
+  int chunk = 256;         // consecutive block rows processed by one CTA
+  int warps = 4;           // warps per CTA of the solves (4, 8 or 16)
   long long spin_ns = kDefaultSpinNs;
   int skip_row = -1;       // test hook: this row of the lower solve is never published
 };
@@ -98,6 +103,9 @@ int launch_backfill(const bilu_pattern* p, int32_t b, const double* a_vals, doub
 int launch_factor(const bilu_pattern* p, int32_t b, double* f, int32_t* header, int32_t* done,
                   void* stream);
 int launch_scale_upper(const bilu_pattern* p, int32_t b, double* f, void* stream);
+int launch_backfill_f32(const bilu_pattern* p, int32_t b, const double* a_vals, float* f, void* stream);
+int launch_factor_f32(const bilu_pattern* p, int32_t b, float* f, int32_t* header, int32_t* done, void* stream);
+int launch_scale_upper_f32(const bilu_pattern* p, int32_t b, float* f, void* stream);
 
 size_t apply_workspace_bytes(int32_t n, int32_t b);
 // Builds (host) and uploads the solve schedule for `chunk` rows per chunk.

@@ -57,8 +57,9 @@ struct Waiter {
   long long limit_ns;
   long long t0;
   int* stop_word;  // optional: raised too, so a caller's pipeline stops
-  __device__ __forceinline__ bool give_up(unsigned it) {
-    if ((it & 31u) != 0u) return false;
+  // Checks the abort word and the clock every (mask + 1) polls.
+  __device__ __forceinline__ bool give_up(unsigned it, unsigned mask = 31u) {
+    if ((it & mask) != 0u) return false;
     if (ld_volatile_s32(header + kAbort)) return true;
     if (t0 == 0) t0 = global_ns();
     if (global_ns() - t0 > limit_ns) {
@@ -84,6 +85,52 @@ __device__ __forceinline__ bool wait_value(const double* p, double& out, Waiter&
   }
 }
 
+// Wait until all N values at p hold computed values (each polled with a
+// relaxed load; the N loads of a round are issued together, so a dependency
+// costs one L2 round trip rather than N); false if the wait was abandoned.
+template <int N>
+__device__ __forceinline__ bool wait_values(const double* p, double (&out)[N], Waiter& w) {
+  w.t0 = 0;
+  for (unsigned it = 1;; ++it) {
+    unsigned long long u[N];
+#pragma unroll
+    for (int q = 0; q < N; ++q) u[q] = ld_relaxed_u64(p + q);
+    bool all = true;
+#pragma unroll
+    for (int q = 0; q < N; ++q) all = all && (u[q] != kPending);
+    if (all) {
+#pragma unroll
+      for (int q = 0; q < N; ++q) out[q] = __longlong_as_double((long long)u[q]);
+      return true;
+    }
+    if (w.give_up(it)) return false;
+  }
+}
+
+// Wait until all N values in this CTA's shared memory at p hold computed
+// values (volatile 64-bit loads: each value is its own ready flag, so no
+// fence is needed); false if the wait was abandoned.  The abort word and the
+// clock are consulted only every 1024 polls: a shared-memory poll is short.
+template <int N>
+__device__ __forceinline__ bool wait_values_shared(const double* p, double (&out)[N], Waiter& w) {
+  w.t0 = 0;
+  const volatile unsigned long long* v = reinterpret_cast<const volatile unsigned long long*>(p);
+  for (unsigned it = 1;; ++it) {
+    unsigned long long u[N];
+#pragma unroll
+    for (int q = 0; q < N; ++q) u[q] = v[q];
+    bool all = true;
+#pragma unroll
+    for (int q = 0; q < N; ++q) all = all && (u[q] != kPending);
+    if (all) {
+#pragma unroll
+      for (int q = 0; q < N; ++q) out[q] = __longlong_as_double((long long)u[q]);
+      return true;
+    }
+    if (w.give_up(it, 1023u)) return false;
+  }
+}
+
 // Wait until *flag != 0 (acquire); false if the wait was abandoned.
 __device__ __forceinline__ bool wait_flag(const int* flag, Waiter& w) {
   w.t0 = 0;
@@ -106,12 +153,13 @@ __device__ __forceinline__ void st_release_cta_shared_s32(int* p, int v) {
 }
 
 // Wait until a shared-memory flag of this CTA equals `want` (acquire, CTA
-// scope); false if the wait was abandoned.
+// scope); false if the wait was abandoned.  The abort word (a global load)
+// and the clock are consulted every 1024 polls only.
 __device__ __forceinline__ bool wait_local_flag(const int* flag, int want, Waiter& w) {
   w.t0 = 0;
   for (unsigned it = 1;; ++it) {
     if (ld_acquire_cta_shared_s32(flag) == want) return true;
-    if (w.give_up(it)) return false;
+    if (w.give_up(it, 1023u)) return false;
   }
 }
 

@@ -30,14 +30,15 @@ namespace bilu {
 namespace {
 
 
+template <typename TV>
 __global__ void backfill_kernel(long long total, int bb, const int32_t* __restrict__ slot_src,
-                                const double* __restrict__ a, double* __restrict__ f) {
+                                const double* __restrict__ a, TV* __restrict__ f) {
   const long long stride = (long long)gridDim.x * blockDim.x;
   for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < total; q += stride) {
     const long long slot = q / bb;
     const int e = (int)(q - slot * bb);
     const int32_t src = __ldg(slot_src + slot);
-    f[q] = src >= 0 ? __ldg(a + (size_t)src * bb + e) : 0.0;
+    f[q] = src >= 0 ? (TV)__ldg(a + (size_t)src * bb + e) : TV(0);
   }
 }
 
@@ -59,37 +60,37 @@ struct FactorCap {
   static constexpr int WINT = RC + 32;                 // ints per warp
 };
 
-template <int B>
+template <int B, typename TV>
 size_t factor_smem_bytes(int chunk) {
-  return (size_t)FactorCap<B>::W * FactorCap<B>::WDBL * sizeof(double) +
+  return (size_t)FactorCap<B>::W * FactorCap<B>::WDBL * sizeof(TV) +
          ((size_t)2 * chunk + (size_t)FactorCap<B>::W * FactorCap<B>::WINT) * sizeof(int);
 }
 
-template <int B>
+template <int B, typename TV>
 __global__ void __launch_bounds__(FactorCap<B>::W * 32) factor_kernel(
-    int32_t n, int32_t chunk, int32_t nchunks, const int32_t* __restrict__ ord,
+    int32_t n, int32_t chunk, int32_t nchunks, const int32_t* __restrict__ ord, const int32_t* __restrict__ tick,
     const int32_t* __restrict__ lrp, const int32_t* __restrict__ lci,
-    const int32_t* __restrict__ urp, const int32_t* __restrict__ uci, double* f, long long nnz_l,
+    const int32_t* __restrict__ urp, const int32_t* __restrict__ uci, TV* f, long long nnz_l,
     int32_t* header, int32_t* done, long long spin_ns) {
   constexpr int BB = B * B;
   constexpr int H = (BB + 31) / 32;
   constexpr int RC = FactorCap<B>::RC;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  double* wd = reinterpret_cast<double*>(smem_raw) + (size_t)warp * FactorCap<B>::WDBL;
-  double* rowv = wd;             // RC blocks of the row being factored
-  double* dp = rowv + RC * BB;   // D_p^{-1}
-  double* aip = dp + BB;         // scaled A_ip
-  double* aug = aip + BB;        // [D_i | I] for Gauss-Jordan
-  int* ib = reinterpret_cast<int*>(reinterpret_cast<double*>(smem_raw) + (size_t)FactorCap<B>::W * FactorCap<B>::WDBL);
+  TV* wd = reinterpret_cast<TV*>(smem_raw) + (size_t)warp * FactorCap<B>::WDBL;
+  TV* rowv = wd;             // RC blocks of the row being factored
+  TV* dp = rowv + RC * BB;   // D_p^{-1}
+  TV* aip = dp + BB;         // scaled A_ip
+  TV* aug = aip + BB;        // [D_i | I] for Gauss-Jordan
+  int* ib = reinterpret_cast<int*>(reinterpret_cast<TV*>(smem_raw) + (size_t)FactorCap<B>::W * FactorCap<B>::WDBL);
   int* fl = ib;                  // chunk-local ready flags (value = chunk id)
   int* s_i = fl + chunk;         // rows of the chunk in local-level order
   int* cols = s_i + chunk + warp * FactorCap<B>::WINT;  // column of each staged slot
   int* dstv = cols + RC;         // destination slot per U_p entry of a batch
   __shared__ int s_c;
-  double* L = f;
-  double* D = f + (size_t)nnz_l * BB;
-  double* U = D + (size_t)n * BB;
+  TV* L = f;
+  TV* D = f + (size_t)nnz_l * BB;
+  TV* U = D + (size_t)n * BB;
   for (int q = tid; q < chunk; q += blockDim.x) fl[q] = -1;
   Waiter w{header, spin_ns, 0, nullptr};
   bool dead = false;
@@ -98,7 +99,7 @@ __global__ void __launch_bounds__(FactorCap<B>::W * 32) factor_kernel(
     if (tid == 0) {
       int cc = atomicAdd(header + kTicketF, 1);
       if (ld_volatile_s32(header + kAbort)) cc = nchunks;
-      s_c = cc;
+      s_c = cc < nchunks ? tick[cc] : nchunks;
     }
     __syncthreads();
     const int c = s_c;
@@ -115,7 +116,7 @@ __global__ void __launch_bounds__(FactorCap<B>::W * 32) factor_kernel(
       const int nrow = nl + 1 + nu;
       const bool staged = nrow <= RC;
       // slot k of row i: L blocks (k < nl), the pivot block (k == nl), U blocks
-      auto blk = [&](int k) -> double* {
+      auto blk = [&](int k) -> TV* {
         if (staged) return rowv + k * BB;
         if (k < nl) return L + (size_t)(lb + k) * BB;
         if (k == nl) return D + (size_t)i * BB;
@@ -164,7 +165,7 @@ __global__ void __launch_bounds__(FactorCap<B>::W * 32) factor_kernel(
         // operands are fetched together (one memory round trip per pivot)
         for (int e = lane; e < BB; e += 32) dp[e] = D[(size_t)p * BB + e];
         constexpr int NPRE = 4;
-        double upre[NPRE][B];
+        TV upre[NPRE][B];
         {
           const int cnt0 = min(32, pe - pb);
 #pragma unroll
@@ -172,21 +173,21 @@ __global__ void __launch_bounds__(FactorCap<B>::W * 32) factor_kernel(
             const int wk = lane + 32 * h;
             if (wk < cnt0 * BB) {
               const int sidx = wk / BB, e = wk - (wk / BB) * BB;
-              const double* upj = U + (size_t)(pb + sidx) * BB + (e / B) * B;
+              const TV* upj = U + (size_t)(pb + sidx) * BB + (e / B) * B;
 #pragma unroll
               for (int m = 0; m < B; ++m) upre[h][m] = upj[m];
             }
           }
         }
         __syncwarp();
-        double* a = blk(k);
-        double nv[H];
+        TV* a = blk(k);
+        TV nv[H];
 #pragma unroll
         for (int h = 0; h < H; ++h) {
           const int e = lane + 32 * h;
           if (e < BB) {
             const int r = e % B, cc = e / B;
-            double s = 0.0;
+            TV s = TV(0);
 #pragma unroll
             for (int m = 0; m < B; ++m) s = fma(a[m * B + r], dp[cc * B + m], s);
             nv[h] = s;
@@ -218,7 +219,7 @@ __global__ void __launch_bounds__(FactorCap<B>::W * 32) factor_kernel(
                 const int d = dstv[sidx];
                 if (d >= 0) {
                   const int r = e % B;
-                  double s = 0.0;
+                  TV s = TV(0);
 #pragma unroll
                   for (int m = 0; m < B; ++m) s = fma(aip[m * B + r], upre[h][m], s);
                   blk(d)[e] -= s;
@@ -232,8 +233,8 @@ __global__ void __launch_bounds__(FactorCap<B>::W * 32) factor_kernel(
             const int d = dstv[sidx];
             if (d >= 0) {
               const int r = e % B, cc = e / B;
-              const double* upj = U + (size_t)(s0 + sidx) * BB + cc * B;
-              double s = 0.0;
+              const TV* upj = U + (size_t)(s0 + sidx) * BB + cc * B;
+              TV s = TV(0);
 #pragma unroll
               for (int m = 0; m < B; ++m) s = fma(aip[m * B + r], upj[m], s);
               blk(d)[e] -= s;
@@ -245,10 +246,10 @@ __global__ void __launch_bounds__(FactorCap<B>::W * 32) factor_kernel(
       if (dead) break;
       // D_i^{-1} by Gauss-Jordan with partial pivoting on [D_i | I].
       {
-        const double* di = blk(nl);
+        const TV* di = blk(nl);
         for (int e = lane; e < 2 * BB; e += 32) {
           const int q = e / B, r = e % B;
-          aug[e] = q < B ? di[e] : (r == q - B ? 1.0 : 0.0);
+          aug[e] = q < B ? di[e] : (r == q - B ? TV(1) : TV(0));
         }
       }
       __syncwarp();
@@ -257,31 +258,31 @@ __global__ void __launch_bounds__(FactorCap<B>::W * 32) factor_kernel(
       bad = __any_sync(kFull, bad);
       for (int cc = 0; cc < B && !bad; ++cc) {
         int pr = cc;
-        double best = fabs(aug[cc * B + cc]);
+        TV best = fabs(aug[cc * B + cc]);
 #pragma unroll
         for (int r = cc + 1; r < B; ++r) {
-          const double v = fabs(aug[cc * B + r]);
+          const TV v = fabs(aug[cc * B + r]);
           if (v > best) { best = v; pr = r; }
         }
-        if (!(best > 0.0)) { bad = true; break; }
-        const double piv = aug[cc * B + pr];
+        if (!(best > TV(0))) { bad = true; break; }
+        const TV piv = aug[cc * B + pr];
         __syncwarp();
         if (lane < 2 * B) {
-          double* col = aug + lane * B;
-          if (pr != cc) { const double tmp = col[cc]; col[cc] = col[pr]; col[pr] = tmp; }
+          TV* col = aug + lane * B;
+          if (pr != cc) { const TV tmp = col[cc]; col[cc] = col[pr]; col[pr] = tmp; }
           col[cc] = col[cc] / piv;
         }
         __syncwarp();
-        double fr[B];
+        TV fr[B];
 #pragma unroll
         for (int r = 0; r < B; ++r) fr[r] = aug[cc * B + r];
         __syncwarp();
         if (lane < 2 * B) {
-          double* col = aug + lane * B;
-          const double pc = col[cc];
+          TV* col = aug + lane * B;
+          const TV pc = col[cc];
 #pragma unroll
           for (int r = 0; r < B; ++r)
-            if (r != cc && fr[r] != 0.0) col[r] = fma(-fr[r], pc, col[r]);
+            if (r != cc && fr[r] != TV(0)) col[r] = fma(-fr[r], pc, col[r]);
         }
         __syncwarp();
       }
@@ -310,28 +311,28 @@ __global__ void __launch_bounds__(FactorCap<B>::W * 32) factor_kernel(
 }
 
 // Eq. 5: U'_ij = D_i^{-1} U_ij, one warp per block row.
-template <int B>
+template <int B, typename TV>
 __global__ void __launch_bounds__(128) scale_upper_kernel(int32_t n, const int32_t* __restrict__ urp,
-                                                          const double* __restrict__ dinv,
-                                                          double* __restrict__ u) {
+                                                          const TV* __restrict__ dinv,
+                                                          TV* __restrict__ u) {
   constexpr int BB = B * B;
   constexpr int H = (BB + 31) / 32;
-  __shared__ double s_d[4][BB];
+  __shared__ TV s_d[4][BB];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  double* d = s_d[wib];
+  TV* d = s_d[wib];
   const long long nw = (long long)gridDim.x * 4;
   for (long long i = (long long)blockIdx.x * 4 + wib; i < n; i += nw) {
     for (int e = lane; e < BB; e += 32) d[e] = dinv[(size_t)i * BB + e];
     __syncwarp();
     for (int t = urp[i]; t < urp[i + 1]; ++t) {
-      double* blk = u + (size_t)t * BB;
-      double nv[H];
+      TV* blk = u + (size_t)t * BB;
+      TV nv[H];
 #pragma unroll
       for (int h = 0; h < H; ++h) {
         const int e = lane + 32 * h;
         if (e < BB) {
           const int r = e % B, c = e / B;
-          double s = 0.0;
+          TV s = TV(0);
 #pragma unroll
           for (int m = 0; m < B; ++m) s = fma(d[m * B + r], blk[c * B + m], s);
           nv[h] = s;
@@ -356,19 +357,19 @@ int device_sms() {
   return sms > 0 ? sms : 1;
 }
 
-}  // namespace
-
-int launch_backfill(const bilu_pattern* p, int32_t b, const double* a_vals, double* f, void* stream) {
+template <typename TV>
+int launch_backfill_t(const bilu_pattern* p, int32_t b, const double* a_vals, TV* f, void* stream) {
   const long long total = p->nslots() * (long long)b * b;
   if (total == 0) return 0;
   const int blocks = (int)std::min<long long>((total + 255) / 256, (long long)device_sms() * 16);
   ProfScope ps(BILU_PROF_BACKFILL, stream);
-  backfill_kernel<<<blocks, 256, 0, (cudaStream_t)stream>>>(total, b * b, p->d_slot_src, a_vals, f);
+  backfill_kernel<TV><<<blocks, 256, 0, (cudaStream_t)stream>>>(total, b * b, p->d_slot_src, a_vals, f);
   return (int)cudaGetLastError();
 }
 
-int launch_factor(const bilu_pattern* p, int32_t b, double* f, int32_t* header, int32_t* done,
-                  void* stream) {
+template <typename TV>
+int launch_factor_t(const bilu_pattern* p, int32_t b, TV* f, int32_t* header, int32_t* done,
+                    void* stream) {
   cudaStream_t s = (cudaStream_t)stream;
   const int32_t n = p->n;
   const int sms = device_sms();
@@ -382,37 +383,59 @@ int launch_factor(const bilu_pattern* p, int32_t b, double* f, int32_t* header, 
   const int nchunks = (n + chunk - 1) / chunk;
   const long long spin = trisolve_config().spin_ns;
   BILU_DISPATCH_B(b, {
-    const size_t smem = factor_smem_bytes<B>(chunk);
+    const size_t smem = factor_smem_bytes<B, TV>(chunk);
     static int last_chunk = -1, per_sm = 1;
     if (last_chunk != chunk) {
-      cudaFuncSetAttribute(factor_kernel<B>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+      cudaFuncSetAttribute(factor_kernel<B, TV>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)std::max<size_t>(smem, 48 * 1024));
       int q = 0;
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&q, factor_kernel<B>, FactorCap<B>::W * 32, smem);
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&q, factor_kernel<B, TV>, FactorCap<B>::W * 32, smem);
       per_sm = q < 1 ? 1 : q;
       last_chunk = chunk;
     }
     const int grid = std::max(1, std::min(nchunks, per_sm * sms));
     ProfScope ps(BILU_PROF_FACTOR, stream);
-    factor_kernel<B><<<grid, FactorCap<B>::W * 32, smem, s>>>(n, chunk, nchunks, p->d_ord_l, p->d_lrp, p->d_lci,
+    factor_kernel<B, TV><<<grid, FactorCap<B>::W * 32, smem, s>>>(n, chunk, nchunks, p->d_ord_l, p->d_tick_l, p->d_lrp, p->d_lci,
                                                             p->d_urp, p->d_uci, f, p->nnz_l(), header, done,
                                                             spin);
   });
   return (int)cudaGetLastError();
 }
 
-int launch_scale_upper(const bilu_pattern* p, int32_t b, double* f, void* stream) {
+template <typename TV>
+int launch_scale_upper_t(const bilu_pattern* p, int32_t b, TV* f, void* stream) {
   const int32_t n = p->n;
   if (n == 0 || p->nnz_u() == 0) return 0;
   const size_t bb = (size_t)b * b;
-  const double* dinv = f + (size_t)p->nnz_l() * bb;
-  double* u = f + ((size_t)p->nnz_l() + n) * bb;
+  const TV* dinv = f + (size_t)p->nnz_l() * bb;
+  TV* u = f + ((size_t)p->nnz_l() + n) * bb;
   const int grid = std::max(1, std::min((n + 3) / 4, device_sms() * 16));
   BILU_DISPATCH_B(b, {
     ProfScope ps(BILU_PROF_SCALE_UPPER, stream);
-    scale_upper_kernel<B><<<grid, 128, 0, (cudaStream_t)stream>>>(n, p->d_urp, dinv, u);
+    scale_upper_kernel<B, TV><<<grid, 128, 0, (cudaStream_t)stream>>>(n, p->d_urp, dinv, u);
   });
   return (int)cudaGetLastError();
+}
+
+}  // namespace
+
+int launch_backfill(const bilu_pattern* p, int32_t b, const double* a_vals, double* f, void* stream) {
+  return launch_backfill_t<double>(p, b, a_vals, f, stream);
+}
+int launch_factor(const bilu_pattern* p, int32_t b, double* f, int32_t* header, int32_t* done, void* stream) {
+  return launch_factor_t<double>(p, b, f, header, done, stream);
+}
+int launch_scale_upper(const bilu_pattern* p, int32_t b, double* f, void* stream) {
+  return launch_scale_upper_t<double>(p, b, f, stream);
+}
+int launch_backfill_f32(const bilu_pattern* p, int32_t b, const double* a_vals, float* f, void* stream) {
+  return launch_backfill_t<float>(p, b, a_vals, f, stream);
+}
+int launch_factor_f32(const bilu_pattern* p, int32_t b, float* f, int32_t* header, int32_t* done, void* stream) {
+  return launch_factor_t<float>(p, b, f, header, done, stream);
+}
+int launch_scale_upper_f32(const bilu_pattern* p, int32_t b, float* f, void* stream) {
+  return launch_scale_upper_t<float>(p, b, f, stream);
 }
 
 }  // namespace bilu

@@ -219,6 +219,10 @@ namespace bilu {
 // chunk it depends on (0 if none), i.e. Eq. 4 restricted to the chunk; rows
 // are listed by (local level, row) for L and (local level, descending row) for
 // U'.  Chunk c occupies positions [c*chunk, c*chunk + len) of ord_l / ord_u.
+// Tickets hand chunks out by their level in the chunk dependency graph (a
+// chunk depends on every chunk holding a row one of its rows depends on), then
+// by chunk index, so a chunk only ever waits on chunks of smaller tickets and
+// the chunks resident at any time form a wavefront of nearly ready ones.
 void build_schedule(bilu_pattern* p, int32_t chunk) {
   const int32_t n = p->n;
   p->ord_l.assign((size_t)n, 0);
@@ -254,6 +258,34 @@ void build_schedule(bilu_pattern* p, int32_t chunk) {
     std::sort(key.begin(), key.end());
     for (size_t q = 0; q < key.size(); ++q) p->ord_u[(size_t)c * chunk + q] = -key[q].second;
   }
+  // chunk dependency levels and ticket orders
+  auto ticket_order = [&](bool upper, std::vector<int32_t>& tick) {
+    std::vector<int32_t> clev((size_t)nchunks, 0);
+    std::vector<std::pair<int32_t, int32_t>> ck;
+    for (int32_t c = 0; c < nchunks; ++c) {
+      int32_t lo, hi;
+      if (!upper) { lo = c * chunk; hi = std::min(n, lo + chunk); }
+      else { hi = n - c * chunk; lo = std::max(0, hi - chunk); }
+      int32_t l = 0;
+      for (int32_t i = lo; i < hi; ++i) {
+        const std::vector<int32_t>& rpv = upper ? p->urp : p->lrp;
+        const std::vector<int32_t>& civ = upper ? p->uci : p->lci;
+        for (int32_t t = rpv[i]; t < rpv[i + 1]; ++t) {
+          const int32_t j = civ[t];
+          if (j >= lo && j < hi) continue;
+          const int32_t cj = upper ? (n - 1 - j) / chunk : j / chunk;
+          l = std::max(l, clev[cj] + 1);
+        }
+      }
+      clev[c] = l;
+      ck.emplace_back(l, c);
+    }
+    std::sort(ck.begin(), ck.end());
+    tick.resize((size_t)nchunks);
+    for (int32_t q = 0; q < nchunks; ++q) tick[q] = ck[q].second;
+  };
+  ticket_order(false, p->tick_l);
+  ticket_order(true, p->tick_u);
   p->sched_chunk = chunk;
 }
 

@@ -12,16 +12,19 @@
 //    ticket;
 //  * inside a chunk the host lists the rows by local dependency level (Eq. 4
 //    restricted to the chunk); the CTA's warps take rows round-robin in that
-//    order, and a dependency inside the chunk is read from shared memory after
-//    an acquire on the row's shared-memory ready flag (release by the writing
-//    lane).  In natural order most dependencies of a grid row lie within a
+//    order.  In natural order most dependencies of a grid row lie within a
 //    few grid lines, i.e. inside its chunk;
-//  * a dependency outside the chunk is read from global memory, waiting until
-//    it no longer holds the "pending" bit pattern: the value is its own ready
-//    flag (no separate flag, no fence, one L2 round trip);
-//  * the column indices and values of a warp's next row, and optimistic
-//    reads of its dependencies outside the chunk, are loaded into registers
-//    before the current row's waits start;
+//  * every value doubles as its own ready flag: a slot holds the "pending"
+//    bit pattern (a signalling-NaN payload no arithmetic produces) until the
+//    value is stored.  A dependency inside the chunk is polled in shared
+//    memory (slots reset to pending when the chunk starts), one outside the
+//    chunk in global memory (one L2 round trip per poll).  No separate flag,
+//    no fence, no acquire on the hot path;
+//  * loads run ahead of the dependency chain in two stages: the column
+//    indices and values (and the row's own operands) of the row a warp will
+//    solve two turns later, and optimistic reads of the next row's
+//    dependencies outside the chunk (which need those column indices), are
+//    issued before the current row's waits start;
 //  * forward progress: a row only waits on rows of earlier positions in its
 //    chunk or of earlier tickets, all held by running warps; every wait is
 //    bounded and gives up with BILU_ERR_TIMEOUT (never a trap), and no warp
@@ -48,7 +51,6 @@ TrisolveConfig& trisolve_config() {
 
 namespace {
 
-constexpr int kTriWarps = 8;
 
 __global__ void apply_prep_kernel(double* y, long long m, int32_t* header, const int32_t* stop) {
   // Each apply starts with a clean header: its status is its own.
@@ -77,16 +79,18 @@ struct RowPre {
   double yi[B];              // U': y_i[q]
 };
 
+// Stage A of the prefetch: the row, its first block (column and values) and
+// its own operands.
 template <int B, bool UPPER, typename TV>
 __device__ __forceinline__ void fetch_row(RowPre<B, UPPER, TV>& p, int pos, int len, const int* s_i,
                                           const int* s_beg, const int* s_end,
                                           const int32_t* __restrict__ ci, const TV* __restrict__ vals,
-                                          const TV* __restrict__ dinv, const double* rhs,
-                                          const double* out, int lo, int hi, int g, int rr, bool act,
-                                          int lane) {
-  if (pos >= len) {
+                                          const TV* __restrict__ dinv, const double* rhs, int g, int rr,
+                                          bool act, int lane) {
+  if (pos >= len) {  // past the chunk's end: nothing to fetch, no dependency to read
     p.i = -1;
     p.beg = p.end = 0;
+    p.j = -1;
     return;
   }
   p.i = s_i[pos];
@@ -99,11 +103,6 @@ __device__ __forceinline__ void fetch_row(RowPre<B, UPPER, TV>& p, int pos, int 
     const TV* a = vals + (size_t)t * (B * B) + rr;
 #pragma unroll
     for (int q = 0; q < B; ++q) p.av[q] = __ldg(a + q * B);
-    // a dependency outside the chunk is usually final already: read it now
-    // (relaxed); if it still holds the pending pattern it is waited for later
-    const bool remote = p.j < lo || p.j >= hi;
-#pragma unroll
-    for (int q = 0; q < B; ++q) p.yv[q] = remote ? ld_relaxed_u64(out + (size_t)p.j * B + q) : kPending;
   }
   if (lane < B) {
     if (!UPPER) {
@@ -119,17 +118,25 @@ __device__ __forceinline__ void fetch_row(RowPre<B, UPPER, TV>& p, int pos, int 
   }
 }
 
+// Stage B: a dependency outside the chunk is usually final already: read it
+// now (relaxed); if it still holds the pending pattern it is waited for later.
 template <int B, bool UPPER, typename TV>
+__device__ __forceinline__ void fetch_deps(RowPre<B, UPPER, TV>& p, const double* out, int lo, int hi) {
+  const bool remote = p.j >= 0 && (p.j < lo || p.j >= hi);
+#pragma unroll
+  for (int q = 0; q < B; ++q) p.yv[q] = remote ? ld_relaxed_u64(out + (size_t)p.j * B + q) : kPending;
+}
+
+template <int B, bool UPPER, typename TV, int kTriWarps>
 __global__ void __launch_bounds__(kTriWarps * 32) tri_solve_kernel(
     int32_t n, int32_t chunk, int32_t nchunks, const int32_t* __restrict__ rp,
     const int32_t* __restrict__ ci, const TV* __restrict__ vals, const TV* __restrict__ dinv,
-    const int32_t* __restrict__ ord, const double* rhs, double* out, double* pend_out,
-    int32_t* header, long long spin_ns, int32_t skip_row, int32_t* stop) {
+    const int32_t* __restrict__ ord, const int32_t* __restrict__ tick, const double* rhs, double* out,
+    double* pend_out, int32_t* header, long long spin_ns, int32_t skip_row, int32_t* stop) {
   constexpr int G = groups_for(B);
   extern __shared__ __align__(16) unsigned char smem_raw[];
   double* yl = reinterpret_cast<double*>(smem_raw);
-  int* fl = reinterpret_cast<int*>(yl + (size_t)chunk * B);
-  int* s_i = fl + chunk;
+  int* s_i = reinterpret_cast<int*>(yl + (size_t)chunk * B);
   int* s_beg = s_i + chunk;
   int* s_end = s_beg + chunk;
   __shared__ int s_c;
@@ -137,7 +144,6 @@ __global__ void __launch_bounds__(kTriWarps * 32) tri_solve_kernel(
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int g = lane / B, rr = lane - (lane / B) * B;
   const bool act = g < G;
-  for (int q = tid; q < chunk; q += blockDim.x) fl[q] = -1;
   Waiter w{header, spin_ns, 0, stop};
   bool dead = false;
   for (;;) {
@@ -145,7 +151,7 @@ __global__ void __launch_bounds__(kTriWarps * 32) tri_solve_kernel(
     if (tid == 0) {
       int cc = atomicAdd(header + (UPPER ? kTicketU : kTicketL), 1);
       if (ld_volatile_s32(header + kAbort)) cc = nchunks;
-      s_c = cc;
+      s_c = cc < nchunks ? tick[cc] : nchunks;
     }
     __syncthreads();
     const int c = s_c;
@@ -166,13 +172,17 @@ __global__ void __launch_bounds__(kTriWarps * 32) tri_solve_kernel(
       s_beg[q] = rp[i];
       s_end[q] = rp[i + 1];
     }
+    for (int q = tid; q < len * B; q += blockDim.x) reinterpret_cast<unsigned long long*>(yl)[q] = kPending;
     __syncthreads();
-    RowPre<B, UPPER, TV> cur, nxt;
-    fetch_row<B, UPPER, TV>(cur, warp, len, s_i, s_beg, s_end, ci, vals, dinv, rhs, out, lo, hi, g, rr, act,
+    RowPre<B, UPPER, TV> cur, nx1, nx2;
+    fetch_row<B, UPPER, TV>(cur, warp, len, s_i, s_beg, s_end, ci, vals, dinv, rhs, g, rr, act, lane);
+    fetch_deps<B, UPPER, TV>(cur, out, lo, hi);
+    fetch_row<B, UPPER, TV>(nx1, warp + kTriWarps, len, s_i, s_beg, s_end, ci, vals, dinv, rhs, g, rr, act,
                             lane);
     for (int pos = warp; pos < len && !dead; pos += kTriWarps) {
-      fetch_row<B, UPPER, TV>(nxt, pos + kTriWarps, len, s_i, s_beg, s_end, ci, vals, dinv, rhs, out, lo, hi,
-                              g, rr, act, lane);
+      fetch_row<B, UPPER, TV>(nx2, pos + 2 * kTriWarps, len, s_i, s_beg, s_end, ci, vals, dinv, rhs, g, rr,
+                              act, lane);
+      fetch_deps<B, UPPER, TV>(nx1, out, lo, hi);
       const int i = cur.i;
       TV acc = TV(0);
       bool ok = true;
@@ -200,17 +210,15 @@ __global__ void __launch_bounds__(kTriWarps * 32) tri_solve_kernel(
           }
           double yj[B];
           if (j >= lo && j < hi) {
-            ok = wait_local_flag(fl + (j - lo), c, w);
-            if (ok) {
-#pragma unroll
-              for (int q = 0; q < B; ++q) yj[q] = yl[(j - lo) * B + q];
-            }
+            ok = wait_values_shared<B>(yl + (size_t)(j - lo) * B, yj, w);
           } else {
+            bool have = true;
 #pragma unroll
             for (int q = 0; q < B; ++q) {
-              if (yv[q] != kPending) yj[q] = __longlong_as_double((long long)yv[q]);
-              else if (ok) ok = wait_value(out + (size_t)j * B + q, yj[q], w);
+              have = have && (yv[q] != kPending);
+              yj[q] = __longlong_as_double((long long)yv[q]);
             }
+            if (!have) ok = wait_values<B>(out + (size_t)j * B, yj, w);
           }
           if (ok) {
 #pragma unroll
@@ -234,17 +242,14 @@ __global__ void __launch_bounds__(kTriWarps * 32) tri_solve_kernel(
           for (int q = 0; q < B; ++q) z = fma(cur.d[q], (TV)cur.yi[q], z);
           v = (double)(z - acc);
         }
+        unsigned long long u = (unsigned long long)__double_as_longlong(v);
+        if (u == kPending) u = kQuietNaN;
+        reinterpret_cast<volatile unsigned long long*>(yl)[(size_t)(i - lo) * B + lane] = u;
         if (i != skip_row) publish(out + (size_t)i * B + lane, v);
         if (!UPPER) reinterpret_cast<unsigned long long*>(pend_out)[(size_t)i * B + lane] = kPending;
       }
-      // one lane writes the row's B values to shared memory, then releases its flag
-#pragma unroll
-      for (int q = 0; q < B; ++q) {
-        const double vq = __shfl_sync(kFull, v, q);
-        if (lane == 0) yl[(i - lo) * B + q] = vq;
-      }
-      if (lane == 0) st_release_cta_shared_s32(fl + (i - lo), c);
-      cur = nxt;
+      cur = nx1;
+      nx1 = nx2;
     }
   }
 }
@@ -260,23 +265,46 @@ int sm_count() {
   return cached;
 }
 
-size_t tri_smem_bytes(int chunk, int b) { return (size_t)chunk * (b * sizeof(double) + 4 * sizeof(int)); }
+size_t tri_smem_bytes(int chunk, int b) { return (size_t)chunk * (b * sizeof(double) + 3 * sizeof(int)); }
 
 // Persistent grid: as many CTAs as fit on the device at once (cached per
 // chunk size; the occupancy query is host work worth skipping per launch).
-template <int B, bool UPPER, typename TV>
+template <int B, bool UPPER, typename TV, int kTriWarps>
 int tri_grid(int chunk, int nchunks) {
   static int last_chunk = -1, last_per_sm = 1;
   if (chunk != last_chunk) {
     const size_t smem = tri_smem_bytes(chunk, B);
-    cudaFuncSetAttribute(tri_solve_kernel<B, UPPER, TV>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaFuncSetAttribute(tri_solve_kernel<B, UPPER, TV, kTriWarps>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)std::max<size_t>(smem, 48 * 1024));
     int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tri_solve_kernel<B, UPPER, TV>, kTriWarps * 32, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tri_solve_kernel<B, UPPER, TV, kTriWarps>,
+                                                  kTriWarps * 32, smem);
     last_per_sm = per_sm < 1 ? 1 : per_sm;
     last_chunk = chunk;
   }
   return std::max(1, std::min(nchunks, last_per_sm * sm_count()));
+}
+
+template <int B, typename TV, int W>
+void launch_solves(const bilu_pattern* p, int chunk, int nchunks, size_t smem, const TV* L, const TV* Dinv,
+                   const TV* U, const double* r, double* y, double* x, int32_t* header, const TrisolveConfig& cfg,
+                   int32_t* stop, void* stream) {
+  cudaStream_t s = (cudaStream_t)stream;
+  const int32_t n = p->n;
+  {
+    const int grid = tri_grid<B, false, TV, W>(chunk, nchunks);
+    ProfScope ps(BILU_PROF_LOWER, stream);
+    tri_solve_kernel<B, false, TV, W><<<grid, W * 32, smem, s>>>(n, chunk, nchunks, p->d_lrp, p->d_lci, L,
+                                                                 nullptr, p->d_ord_l, p->d_tick_l, r, y, x,
+                                                                 header, cfg.spin_ns, cfg.skip_row, stop);
+  }
+  {
+    const int grid = tri_grid<B, true, TV, W>(chunk, nchunks);
+    ProfScope ps(BILU_PROF_UPPER, stream);
+    tri_solve_kernel<B, true, TV, W><<<grid, W * 32, smem, s>>>(n, chunk, nchunks, p->d_urp, p->d_uci, U, Dinv,
+                                                                p->d_ord_u, p->d_tick_u, y, x, nullptr, header,
+                                                                cfg.spin_ns, -1, stop);
+  }
 }
 
 template <typename TV>
@@ -303,20 +331,12 @@ int launch_apply_t(const bilu_pattern* p, int32_t b, const TV* f, const double* 
     apply_prep_kernel<<<prep_blocks, 256, 0, s>>>(y, m, header, stop);
   }
   BILU_DISPATCH_B(b, {
-    {
-      const int grid = tri_grid<B, false, TV>(chunk, nchunks);
-      ProfScope ps(BILU_PROF_LOWER, stream);
-      tri_solve_kernel<B, false, TV><<<grid, kTriWarps * 32, smem, s>>>(
-          n, chunk, nchunks, p->d_lrp, p->d_lci, L, nullptr, p->d_ord_l, r, y, x, header, cfg.spin_ns,
-          cfg.skip_row, stop);
-    }
-    {
-      const int grid = tri_grid<B, true, TV>(chunk, nchunks);
-      ProfScope ps(BILU_PROF_UPPER, stream);
-      tri_solve_kernel<B, true, TV><<<grid, kTriWarps * 32, smem, s>>>(
-          n, chunk, nchunks, p->d_urp, p->d_uci, U, Dinv, p->d_ord_u, y, x, nullptr, header, cfg.spin_ns, -1,
-          stop);
-    }
+    if (cfg.warps == 16)
+      launch_solves<B, TV, 16>(p, chunk, nchunks, smem, L, Dinv, U, r, y, x, header, cfg, stop, stream);
+    else if (cfg.warps == 4)
+      launch_solves<B, TV, 4>(p, chunk, nchunks, smem, L, Dinv, U, r, y, x, header, cfg, stop, stream);
+    else
+      launch_solves<B, TV, 8>(p, chunk, nchunks, smem, L, Dinv, U, r, y, x, header, cfg, stop, stream);
   });
   return (int)cudaGetLastError();
 }
@@ -332,8 +352,9 @@ int ensure_schedule(bilu_pattern* p, int32_t chunk) {
   }
   if (p->n == 0) return 0;
   const size_t one = align256(sizeof(int32_t) * (size_t)p->n);
+  const size_t tk = align256(sizeof(int32_t) * p->tick_l.size());
   void* mem = nullptr;
-  if (cudaMalloc(&mem, 2 * one) != cudaSuccess) {
+  if (cudaMalloc(&mem, 2 * one + 2 * tk) != cudaSuccess) {
     cudaGetLastError();
     p->sched_chunk = 0;
     return (int)cudaErrorMemoryAllocation;
@@ -341,8 +362,12 @@ int ensure_schedule(bilu_pattern* p, int32_t chunk) {
   p->d_sched = mem;
   p->d_ord_l = (int32_t*)mem;
   p->d_ord_u = (int32_t*)((char*)mem + one);
+  p->d_tick_l = (int32_t*)((char*)mem + 2 * one);
+  p->d_tick_u = (int32_t*)((char*)mem + 2 * one + tk);
   cudaMemcpy(p->d_ord_l, p->ord_l.data(), sizeof(int32_t) * p->n, cudaMemcpyHostToDevice);
   cudaMemcpy(p->d_ord_u, p->ord_u.data(), sizeof(int32_t) * p->n, cudaMemcpyHostToDevice);
+  cudaMemcpy(p->d_tick_l, p->tick_l.data(), sizeof(int32_t) * p->tick_l.size(), cudaMemcpyHostToDevice);
+  cudaMemcpy(p->d_tick_u, p->tick_u.data(), sizeof(int32_t) * p->tick_u.size(), cudaMemcpyHostToDevice);
   return (int)cudaGetLastError();
 }
 

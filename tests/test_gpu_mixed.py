@@ -111,3 +111,19 @@ def test_bicgstab_mixed_edge_cases(B):
     assert info.status == 5 and info.iters == 3
     with pytest.raises(B.BiluError):
         B.bicgstab_solve_mixed(P, A, vals32, F32, rhs, inner_tol=1.5)
+
+
+@pytest.mark.parametrize("b,k", [(3, 1), (4, 2), (8, 0)])
+def test_factor_f32_close_to_fp64(B, b, k):
+    """The factorization computed in FP32 stays within FP32 rounding growth of
+    the oracle's FP64 factors on these well-conditioned systems."""
+    S = reservoir_system(10, 8, 6, b, sigma=1.0, accum=0.01, seed=b + k)
+    o = OracleRun(S.n, b, S.row_ptr, S.col_idx, S.vals, k)
+    rp, ci, vals, rhs = device_system(S, DEV)
+    P = B.bilu_symbolic(S.n, S.row_ptr, S.col_idx, k).upload()
+    F32, info = B.bilu_factor_f32(P, b, vals)
+    assert info.status == 0
+    Lg, Dg, Ug = (t.double().cpu().numpy() for t in B.factor_sections(P, b, F32))
+    assert rel_maxerr(Lg, o.L()) <= 1e-4
+    assert rel_maxerr(Dg, o.Dinv) <= 1e-4
+    assert rel_maxerr(Ug, o.U()) <= 1e-4
