@@ -23,18 +23,29 @@ extern "C" {
 int bilu_set_trisolve_chunk(int32_t rows);
 int32_t bilu_get_trisolve_chunk(void);
 
+/* Consecutive block rows one CTA owns in the sync-free factorization
+ * (default 512), 1 <= rows <= 1024, else BILU_ERR_ARG.  Its schedule is
+ * separate from the solves' and is rebuilt by the next factorization. */
+int bilu_set_factor_chunk(int32_t rows);
+int32_t bilu_get_factor_chunk(void);
+
 /* Warps per CTA in the triangular solves: 4 (default), 8 or 16, else
  * BILU_ERR_ARG.  More warps per chunk give each row more time to fetch its
  * operands ahead of its dependencies. */
 int bilu_set_trisolve_warps(int32_t warps);
 
-/* Host copy of the chunk-local row order the sync-free solves use for `rows`
- * rows per chunk (the same order bilu_apply builds): chunk c occupies
- * positions [c*rows, c*rows + len) of ord_lower (chunks of ascending rows) and
- * of ord_upper (chunks of descending rows, starting from row n - 1); inside a
- * chunk, rows are listed by their dependency level within the chunk.  Each
- * output holds n entries (caller-allocated).  Host only. */
-int bilu_schedule_export(const bilu_pattern* p, int32_t rows, int32_t* ord_lower, int32_t* ord_upper);
+/* Host copy of the schedule the sync-free solves and the factorization use
+ * for `rows` rows per chunk (the same one bilu_apply builds).
+ *   ord_lower / ord_upper (n entries each): chunk c occupies positions
+ *     [c*rows, c*rows + len) -- chunks of ascending rows for L, of descending
+ *     rows starting from row n - 1 for U'; inside a chunk, rows are listed by
+ *     their dependency level within the chunk.
+ *   tick_lower / tick_upper (ceil(n / rows) entries each, may be NULL): the
+ *     chunk each claim ticket hands out, a topological order of the chunk
+ *     dependency graph.
+ * Outputs are caller-allocated.  Host only. */
+int bilu_schedule_export(const bilu_pattern* p, int32_t rows, int32_t* ord_lower, int32_t* ord_upper,
+                         int32_t* tick_lower, int32_t* tick_upper);
 
 /* Time limit of every bounded dependency wait in the factorization and the
  * triangular solves, in nanoseconds (default 2e9).  >= 1000, else

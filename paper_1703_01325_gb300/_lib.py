@@ -75,13 +75,15 @@ SIGNATURES = {
     "bilu_set_trisolve_chunk": (C.c_int, [C.c_int32]),
     "bilu_get_trisolve_chunk": (C.c_int32, []),
     "bilu_set_trisolve_warps": (C.c_int, [C.c_int32]),
+    "bilu_set_factor_chunk": (C.c_int, [C.c_int32]),
+    "bilu_get_factor_chunk": (C.c_int32, []),
     "bilu_set_spin_limit_ns": (C.c_int, [C.c_int64]),
     "bilu_set_check_every": (C.c_int, [C.c_int32]),
     "bilu_test_withhold_row": (C.c_int, [C.c_int32]),
     "bilu_profile_enable": (C.c_int, [C.c_int32]),
     "bilu_profile_read": (C.c_int, [C.c_int32, C.POINTER(C.c_int64), C.POINTER(C.c_double)]),
     "bilu_launch_count": (C.c_int64, []),
-    "bilu_schedule_export": (C.c_int, [_vp, C.c_int32, _i32p, _i32p]),
+    "bilu_schedule_export": (C.c_int, [_vp, C.c_int32, _i32p, _i32p, _i32p, _i32p]),
 }
 
 PROF_KERNELS = ["spmv", "apply_prep", "lower_solve", "upper_solve", "backfill", "factor",

@@ -87,13 +87,20 @@ class Pattern:
         self.uploaded = True
         return self
 
-    def schedule(self, rows: int):
-        """The chunk-local row orders of the sync-free solves (bilu_schedule_export)."""
+    def schedule(self, rows: int, tickets: bool = False):
+        """The chunk-local row orders of the sync-free solves, and with
+        ``tickets`` the chunk claim orders too (bilu_schedule_export)."""
         n = self.info.n
+        nch = (n + rows - 1) // rows
         lo = np.zeros(max(n, 1), np.int32)
         up = np.zeros(max(n, 1), np.int32)
+        tl = np.zeros(max(nch, 1), np.int32)
+        tu = np.zeros(max(nch, 1), np.int32)
         p = lambda a: a.ctypes.data_as(C.POINTER(C.c_int32))
-        _check(L.load().bilu_schedule_export(self.handle, rows, p(lo), p(up)), "bilu_schedule_export")
+        _check(L.load().bilu_schedule_export(self.handle, rows, p(lo), p(up), p(tl), p(tu)),
+               "bilu_schedule_export")
+        if tickets:
+            return lo[:n], up[:n], tl[:nch], tu[:nch]
         return lo[:n], up[:n]
 
     def factor_bytes(self, b: int) -> int:
@@ -320,6 +327,14 @@ def bilu_set_trisolve_warps(warps: int):
 
 def bilu_get_trisolve_chunk() -> int:
     return int(L.load().bilu_get_trisolve_chunk())
+
+
+def bilu_set_factor_chunk(rows: int):
+    _check(L.load().bilu_set_factor_chunk(rows), "bilu_set_factor_chunk")
+
+
+def bilu_get_factor_chunk() -> int:
+    return int(L.load().bilu_get_factor_chunk())
 
 
 def bilu_set_spin_limit_ns(ns: int):

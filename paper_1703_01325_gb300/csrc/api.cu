@@ -15,6 +15,15 @@ namespace {
 
 bool valid_b(int32_t b) { return b >= 1 && b <= 8; }
 
+// The schedules the factorization and the solves run on, rebuilt (host work
+// plus one device allocation) when the configured chunk size changed.
+int solve_schedule(const bilu_pattern* p) {
+  return ensure_schedule(p, &const_cast<bilu_pattern*>(p)->solve, trisolve_config().chunk, true);
+}
+int factor_schedule(const bilu_pattern* p) {
+  return ensure_schedule(p, &const_cast<bilu_pattern*>(p)->fact, trisolve_config().factor_chunk, false);
+}
+
 int ready(const bilu_pattern* p) {
   if (!p) return BILU_ERR_ARG;
   if (p->n > 0 && !p->d_mem) return BILU_ERR_STATE;
@@ -89,14 +98,17 @@ extern "C" int bilu_pattern_upload(bilu_pattern* p, void* stream) {
   }
   p->d_mem = mem;
   p->device = dev;
-  if (ensure_schedule(p, trisolve_config().chunk) != 0) return BILU_ERR_OOM;
+  if (ensure_schedule(p, &p->solve, trisolve_config().chunk, true) != 0 ||
+      ensure_schedule(p, &p->fact, trisolve_config().factor_chunk, false) != 0)
+    return BILU_ERR_OOM;
   return BILU_OK;
 }
 
 extern "C" void bilu_destroy_pattern(bilu_pattern* p) {
   if (!p) return;
   if (p->d_mem) cudaFree(p->d_mem);
-  if (p->d_sched) cudaFree(p->d_sched);
+  free_schedule(&p->solve);
+  free_schedule(&p->fact);
   delete p;
 }
 
@@ -125,7 +137,7 @@ int factor_impl(const bilu_pattern* p, int32_t b, const double* d_a_vals, TV* d_
   if (st) return st;
   if (p->n > 0 && (!d_a_vals || !d_factors || !d_work)) return BILU_ERR_ARG;
   if (work_bytes < bilu_factor_workspace_bytes(p, b)) return BILU_ERR_STATE;
-  if (ensure_schedule(const_cast<bilu_pattern*>(p), trisolve_config().chunk) != 0) return BILU_ERR_OOM;
+  if (factor_schedule(p) != 0) return BILU_ERR_OOM;
   cudaStream_t s = (cudaStream_t)stream;
   int32_t* header = (int32_t*)d_work;
   int32_t* done = (int32_t*)((char*)d_work + kHeaderBytes);
@@ -187,7 +199,7 @@ extern "C" int bilu_apply(const bilu_pattern* p, int32_t b, const double* d_fact
   if (p->n == 0) return BILU_OK;
   if (!d_factors || !d_r || !d_x || !d_work || (const void*)d_r == (const void*)d_x) return BILU_ERR_ARG;
   if (work_bytes < apply_workspace_bytes(p->n, b)) return BILU_ERR_STATE;
-  if (ensure_schedule(const_cast<bilu_pattern*>(p), trisolve_config().chunk) != 0) return BILU_ERR_OOM;
+  if (solve_schedule(p) != 0) return BILU_ERR_OOM;
   return cuda_status(launch_apply(p, b, d_factors, d_r, d_x, d_work, nullptr, stream));
 }
 
@@ -238,7 +250,7 @@ extern "C" int bicgstab_solve(const bilu_pattern* p, const bilu_bsr* A, const do
       (const void*)d_rhs == (const void*)d_x)
     return BILU_ERR_ARG;
   if (work_bytes < krylov_workspace_bytes(p->n, A->b)) return BILU_ERR_STATE;
-  if (ensure_schedule(const_cast<bilu_pattern*>(p), trisolve_config().chunk) != 0) return BILU_ERR_OOM;
+  if (solve_schedule(p) != 0) return BILU_ERR_OOM;
   return run_bicgstab(p, A, d_factors, d_rhs, d_x, tol, maxit, d_work, stream, info, g_check_every);
 }
 
@@ -262,7 +274,7 @@ extern "C" int bilu_apply_f32(const bilu_pattern* p, int32_t b, const float* d_f
   if (p->n == 0) return BILU_OK;
   if (!d_factors32 || !d_r || !d_x || !d_work || (const void*)d_r == (const void*)d_x) return BILU_ERR_ARG;
   if (work_bytes < apply_workspace_bytes(p->n, b)) return BILU_ERR_STATE;
-  if (ensure_schedule(const_cast<bilu_pattern*>(p), trisolve_config().chunk) != 0) return BILU_ERR_OOM;
+  if (solve_schedule(p) != 0) return BILU_ERR_OOM;
   return cuda_status(launch_apply_f32(p, b, d_factors32, d_r, d_x, d_work, nullptr, stream));
 }
 
@@ -303,7 +315,7 @@ extern "C" int bicgstab_solve_mixed(const bilu_pattern* p, const bilu_bsr* A, co
       (const void*)d_rhs == (const void*)d_x)
     return BILU_ERR_ARG;
   if (work_bytes < krylov_mixed_workspace_bytes(p->n, A->b)) return BILU_ERR_STATE;
-  if (ensure_schedule(const_cast<bilu_pattern*>(p), trisolve_config().chunk) != 0) return BILU_ERR_OOM;
+  if (solve_schedule(p) != 0) return BILU_ERR_OOM;
   return run_bicgstab_mixed(p, A, d_vals32, d_factors32, d_rhs, d_x, tol, maxit, inner_tol, inner_maxit,
                             d_work, stream, info, g_check_every);
 }
@@ -317,6 +329,14 @@ extern "C" int bilu_set_trisolve_chunk(int32_t rows) {
 }
 
 extern "C" int32_t bilu_get_trisolve_chunk(void) { return trisolve_config().chunk; }
+
+extern "C" int bilu_set_factor_chunk(int32_t rows) {
+  if (rows < 1 || rows > 1024) return BILU_ERR_ARG;
+  trisolve_config().factor_chunk = rows;
+  return BILU_OK;
+}
+
+extern "C" int32_t bilu_get_factor_chunk(void) { return trisolve_config().factor_chunk; }
 
 extern "C" int bilu_set_trisolve_warps(int32_t warps) {
   if (warps != 4 && warps != 8 && warps != 16) return BILU_ERR_ARG;
@@ -342,18 +362,15 @@ extern "C" int bilu_test_withhold_row(int32_t row) {
 }
 
 extern "C" int bilu_schedule_export(const bilu_pattern* p, int32_t rows, int32_t* ord_lower,
-                                    int32_t* ord_upper) {
+                                    int32_t* ord_upper, int32_t* tick_lower, int32_t* tick_upper) {
   if (!p || rows < 1 || rows > 1024 || (p->n > 0 && (!ord_lower || !ord_upper))) return BILU_ERR_ARG;
-  bilu_pattern tmp;
-  tmp.n = p->n;
-  tmp.lrp = p->lrp;
-  tmp.lci = p->lci;
-  tmp.urp = p->urp;
-  tmp.uci = p->uci;
-  build_schedule(&tmp, rows);
+  bilu_chunk_schedule tmp;
+  build_schedule(p, rows, true, &tmp);
   if (p->n > 0) {
     std::memcpy(ord_lower, tmp.ord_l.data(), sizeof(int32_t) * (size_t)p->n);
     std::memcpy(ord_upper, tmp.ord_u.data(), sizeof(int32_t) * (size_t)p->n);
+    if (tick_lower) std::memcpy(tick_lower, tmp.tick_l.data(), sizeof(int32_t) * tmp.tick_l.size());
+    if (tick_upper) std::memcpy(tick_upper, tmp.tick_u.data(), sizeof(int32_t) * tmp.tick_u.size());
   }
   return BILU_OK;
 }

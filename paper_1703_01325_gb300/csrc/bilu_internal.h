@@ -10,6 +10,22 @@
 #include "../../include/bilu.h"
 #include "../../include/bilu_tuning.h"
 
+// Sync-free schedule for one chunk size (symbolic.cpp builds it, trisolve.cu
+// uploads it): rows cut into chunks of `chunk` consecutive rows (ascending
+// chunks for L, descending for U'); ord_l / ord_u list each chunk's rows by
+// local dependency level; tick_l / tick_u give the chunk each claim ticket
+// hands out (a topological order of the chunk dependency graph).
+struct bilu_chunk_schedule {
+  int32_t chunk = 0;
+  bool upper = false;  // ord_u / tick_u built too
+  std::vector<int32_t> ord_l, ord_u, tick_l, tick_u;
+  void* d_mem = nullptr;
+  int32_t* d_ord_l = nullptr;
+  int32_t* d_ord_u = nullptr;
+  int32_t* d_tick_l = nullptr;
+  int32_t* d_tick_u = nullptr;
+};
+
 struct bilu_pattern {
   int32_t n = 0;
   int32_t k = 0;
@@ -24,18 +40,9 @@ struct bilu_pattern {
   // Backfill gather map: for every factor slot in [L | D | U] the A block that
   // lands there, or -1 for a fill block (Algorithm 5 steps 3-4).
   std::vector<int32_t> slot_src;
-  // Sync-free solve schedule (see trisolve.cu): rows cut into chunks of
-  // sched_chunk consecutive rows (ascending chunks for L, descending for U');
-  // ord_l / ord_u list each chunk's rows by local dependency level.
-  // tick_l / tick_u: the chunk each ticket hands out, ordered by the chunk's
-  // level in the chunk dependency graph (then chunk index).
-  int32_t sched_chunk = 0;
-  std::vector<int32_t> ord_l, ord_u, tick_l, tick_u;
-  void* d_sched = nullptr;
-  int32_t* d_ord_l = nullptr;
-  int32_t* d_ord_u = nullptr;
-  int32_t* d_tick_l = nullptr;
-  int32_t* d_tick_u = nullptr;
+  // Schedules of the triangular solves and of the factorization (L only);
+  // each has its own chunk size.
+  bilu_chunk_schedule solve, fact;
   // Device copy (bilu_pattern_upload).
   int device = -1;
   void* d_mem = nullptr;
@@ -71,8 +78,9 @@ constexpr long long kDefaultSpinNs = 2000000000LL;  // 2 s
 
 // Tunables of the sync-free triangular solves (see trisolve.cu).
 struct TrisolveConfig {
-  int chunk = 256;         // consecutive block rows processed by one CTA
+  int chunk = 256;         // consecutive block rows one CTA of the solves owns
   int warps = 4;           // warps per CTA of the solves (4, 8 or 16)
+  int factor_chunk = 512;  // consecutive block rows one CTA of the factorization owns
   long long spin_ns = kDefaultSpinNs;
   int skip_row = -1;       // test hook: this row of the lower solve is never published
 };
@@ -108,9 +116,12 @@ int launch_factor_f32(const bilu_pattern* p, int32_t b, float* f, int32_t* heade
 int launch_scale_upper_f32(const bilu_pattern* p, int32_t b, float* f, void* stream);
 
 size_t apply_workspace_bytes(int32_t n, int32_t b);
-// Builds (host) and uploads the solve schedule for `chunk` rows per chunk.
-int ensure_schedule(bilu_pattern* p, int32_t chunk);
-void build_schedule(bilu_pattern* p, int32_t chunk);  // host part (symbolic.cpp)
+// Builds (host) and uploads schedule *s for `chunk` rows per chunk (the U'
+// part only if `upper`); nothing happens if it is current.
+int ensure_schedule(const bilu_pattern* p, bilu_chunk_schedule* s, int32_t chunk, bool upper);
+// Host part (symbolic.cpp).
+void build_schedule(const bilu_pattern* p, int32_t chunk, bool upper, bilu_chunk_schedule* s);
+void free_schedule(bilu_chunk_schedule* s);
 int launch_apply(const bilu_pattern* p, int32_t b, const double* f, const double* r, double* x,
                  void* work, int32_t* stop, void* stream);
 int launch_apply_f32(const bilu_pattern* p, int32_t b, const float* f, const double* r, double* x,

@@ -378,8 +378,8 @@ int launch_factor_t(const bilu_pattern* p, int32_t b, TV* f, int32_t* header, in
     factor_init_kernel<<<std::max(1, std::min((n + 255) / 256, sms * 4)), 256, 0, s>>>(header, done, n);
   }
   if (n == 0) return (int)cudaGetLastError();
-  const int chunk = p->sched_chunk;
-  if (chunk <= 0 || !p->d_sched) return (int)cudaErrorInvalidValue;
+  const int chunk = p->fact.chunk;
+  if (chunk <= 0 || !p->fact.d_mem) return (int)cudaErrorInvalidValue;
   const int nchunks = (n + chunk - 1) / chunk;
   const long long spin = trisolve_config().spin_ns;
   BILU_DISPATCH_B(b, {
@@ -395,7 +395,7 @@ int launch_factor_t(const bilu_pattern* p, int32_t b, TV* f, int32_t* header, in
     }
     const int grid = std::max(1, std::min(nchunks, per_sm * sms));
     ProfScope ps(BILU_PROF_FACTOR, stream);
-    factor_kernel<B, TV><<<grid, FactorCap<B>::W * 32, smem, s>>>(n, chunk, nchunks, p->d_ord_l, p->d_tick_l, p->d_lrp, p->d_lci,
+    factor_kernel<B, TV><<<grid, FactorCap<B>::W * 32, smem, s>>>(n, chunk, nchunks, p->fact.d_ord_l, p->fact.d_tick_l, p->d_lrp, p->d_lci,
                                                             p->d_urp, p->d_uci, f, p->nnz_l(), header, done,
                                                             spin);
   });

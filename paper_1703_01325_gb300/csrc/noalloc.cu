@@ -58,7 +58,7 @@ extern "C" int bilu_apply_noalloc(const bilu_pattern* p, int32_t b, const double
   if (!d_factors || !d_r || !d_x || (const void*)d_r == (const void*)d_x) return BILU_ERR_ARG;
   // The solve order must already exist (bilu_pattern_upload builds it):
   // building it here would allocate.
-  if (p->sched_chunk <= 0 || !p->d_sched) return BILU_ERR_STATE;
+  if (p->solve.chunk <= 0 || !p->solve.upper || !p->solve.d_mem) return BILU_ERR_STATE;
   if (bilu::apply_workspace_bytes(p->n, b) > kNoAllocScratchBytes) return BILU_ERR_STATE;
   void* scratch = nullptr;
   const int st = scratch_for_current_device(&scratch);

@@ -219,14 +219,19 @@ namespace bilu {
 // chunk it depends on (0 if none), i.e. Eq. 4 restricted to the chunk; rows
 // are listed by (local level, row) for L and (local level, descending row) for
 // U'.  Chunk c occupies positions [c*chunk, c*chunk + len) of ord_l / ord_u.
-// Tickets hand chunks out by their level in the chunk dependency graph (a
-// chunk depends on every chunk holding a row one of its rows depends on), then
-// by chunk index, so a chunk only ever waits on chunks of smaller tickets and
-// the chunks resident at any time form a wavefront of nearly ready ones.
-void build_schedule(bilu_pattern* p, int32_t chunk) {
+// Tickets hand chunks out in a topological order of the chunk dependency
+// graph (a chunk depends on every other chunk holding a row one of its rows
+// depends on), so a chunk only ever waits on chunks of smaller tickets.  The
+// order is built by list scheduling: among the chunks whose predecessors are
+// all listed, the next ticket goes to the one whose earliest row has the
+// smallest Eq. 4 level (then the smaller chunk index).  The Eq. 4 level of a
+// row is where it sits on the longest dependency chain, i.e. roughly when it
+// can start, so chunks are claimed in about the order they can run and few
+// resident CTAs sit on chunks that cannot start yet.
+void build_schedule(const bilu_pattern* p, int32_t chunk, bool upper, bilu_chunk_schedule* s) {
   const int32_t n = p->n;
-  p->ord_l.assign((size_t)n, 0);
-  p->ord_u.assign((size_t)n, 0);
+  s->ord_l.assign((size_t)n, 0);
+  s->ord_u.assign(upper ? (size_t)n : 0, 0);
 
   std::vector<int32_t> loc((size_t)std::max(chunk, 1), 0);
   std::vector<std::pair<int32_t, int32_t>> key;
@@ -243,7 +248,8 @@ void build_schedule(bilu_pattern* p, int32_t chunk) {
       key.emplace_back(l, i);
     }
     std::sort(key.begin(), key.end());
-    for (size_t q = 0; q < key.size(); ++q) p->ord_l[(size_t)c * chunk + q] = key[q].second;
+    for (size_t q = 0; q < key.size(); ++q) s->ord_l[(size_t)c * chunk + q] = key[q].second;
+    if (!upper) continue;
     // upper: rows [lo, hi) with hi = n - c*chunk
     hi = n - c * chunk;
     lo = std::max(0, hi - chunk);
@@ -256,37 +262,65 @@ void build_schedule(bilu_pattern* p, int32_t chunk) {
       key.emplace_back(l, -i);
     }
     std::sort(key.begin(), key.end());
-    for (size_t q = 0; q < key.size(); ++q) p->ord_u[(size_t)c * chunk + q] = -key[q].second;
+    for (size_t q = 0; q < key.size(); ++q) s->ord_u[(size_t)c * chunk + q] = -key[q].second;
   }
-  // chunk dependency levels and ticket orders
-  auto ticket_order = [&](bool upper, std::vector<int32_t>& tick) {
-    std::vector<int32_t> clev((size_t)nchunks, 0);
-    std::vector<std::pair<int32_t, int32_t>> ck;
+  // ticket orders (list scheduling over the chunk dependency graph)
+  auto ticket_order = [&](bool up, std::vector<int32_t>& tick) {
+    const std::vector<int32_t>& rpv = up ? p->urp : p->lrp;
+    const std::vector<int32_t>& civ = up ? p->uci : p->lci;
+    const std::vector<int32_t>& lvl = up ? p->lvl_u : p->lvl_l;
+    std::vector<int32_t> prio((size_t)nchunks, 0), indeg((size_t)nchunks, 0), seen((size_t)nchunks, -1);
+    std::vector<int32_t> epred, esucc;  // distinct edges pred -> succ
     for (int32_t c = 0; c < nchunks; ++c) {
       int32_t lo, hi;
-      if (!upper) { lo = c * chunk; hi = std::min(n, lo + chunk); }
+      if (!up) { lo = c * chunk; hi = std::min(n, lo + chunk); }
       else { hi = n - c * chunk; lo = std::max(0, hi - chunk); }
-      int32_t l = 0;
+      int32_t pm = INT32_MAX;
       for (int32_t i = lo; i < hi; ++i) {
-        const std::vector<int32_t>& rpv = upper ? p->urp : p->lrp;
-        const std::vector<int32_t>& civ = upper ? p->uci : p->lci;
+        pm = std::min(pm, lvl.empty() ? 0 : lvl[i]);
         for (int32_t t = rpv[i]; t < rpv[i + 1]; ++t) {
           const int32_t j = civ[t];
           if (j >= lo && j < hi) continue;
-          const int32_t cj = upper ? (n - 1 - j) / chunk : j / chunk;
-          l = std::max(l, clev[cj] + 1);
+          const int32_t cj = up ? (n - 1 - j) / chunk : j / chunk;
+          if (seen[cj] == c) continue;
+          seen[cj] = c;
+          epred.push_back(cj);
+          esucc.push_back(c);
+          ++indeg[c];
         }
       }
-      clev[c] = l;
-      ck.emplace_back(l, c);
+      prio[c] = pm;
     }
-    std::sort(ck.begin(), ck.end());
-    tick.resize((size_t)nchunks);
-    for (int32_t q = 0; q < nchunks; ++q) tick[q] = ck[q].second;
+    // successor lists in CSR form
+    std::vector<int64_t> off((size_t)nchunks + 1, 0);
+    for (int32_t e : epred) ++off[(size_t)e + 1];
+    for (int32_t c = 0; c < nchunks; ++c) off[c + 1] += off[c];
+    std::vector<int32_t> succ(epred.size());
+    {
+      std::vector<int64_t> at(off.begin(), off.end() - 1);
+      for (size_t e = 0; e < epred.size(); ++e) succ[at[epred[e]]++] = esucc[e];
+    }
+    std::priority_queue<std::pair<int32_t, int32_t>, std::vector<std::pair<int32_t, int32_t>>,
+                        std::greater<std::pair<int32_t, int32_t>>>
+        ready;
+    for (int32_t c = 0; c < nchunks; ++c)
+      if (indeg[c] == 0) ready.emplace(prio[c], c);
+    tick.clear();
+    tick.reserve((size_t)nchunks);
+    while (!ready.empty()) {
+      const int32_t c = ready.top().second;
+      ready.pop();
+      tick.push_back(c);
+      for (int64_t e = off[c]; e < off[c + 1]; ++e)
+        if (--indeg[succ[e]] == 0) ready.emplace(prio[succ[e]], succ[e]);
+    }
+    // the chunk graph of a triangular pattern is acyclic: every chunk is listed
   };
-  ticket_order(false, p->tick_l);
-  ticket_order(true, p->tick_u);
-  p->sched_chunk = chunk;
+  ticket_order(false, s->tick_l);
+  if (upper) ticket_order(true, s->tick_u);
+  else s->tick_u.clear();
+  s->chunk = chunk;
+  s->upper = upper;
 }
 
 }  // namespace bilu

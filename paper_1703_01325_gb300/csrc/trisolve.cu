@@ -268,41 +268,43 @@ int sm_count() {
 size_t tri_smem_bytes(int chunk, int b) { return (size_t)chunk * (b * sizeof(double) + 3 * sizeof(int)); }
 
 // Persistent grid: as many CTAs as fit on the device at once (cached per
-// chunk size; the occupancy query is host work worth skipping per launch).
+// shared-memory size; the occupancy query is host work worth skipping per
+// launch).
 template <int B, bool UPPER, typename TV, int kTriWarps>
-int tri_grid(int chunk, int nchunks) {
-  static int last_chunk = -1, last_per_sm = 1;
-  if (chunk != last_chunk) {
-    const size_t smem = tri_smem_bytes(chunk, B);
+int tri_grid(size_t smem, int nchunks) {
+  static size_t last_smem = 0;
+  static int last_per_sm = 1;
+  if (smem != last_smem) {
     cudaFuncSetAttribute(tri_solve_kernel<B, UPPER, TV, kTriWarps>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)std::max<size_t>(smem, 48 * 1024));
     int per_sm = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tri_solve_kernel<B, UPPER, TV, kTriWarps>,
                                                   kTriWarps * 32, smem);
     last_per_sm = per_sm < 1 ? 1 : per_sm;
-    last_chunk = chunk;
+    last_smem = smem;
   }
   return std::max(1, std::min(nchunks, last_per_sm * sm_count()));
 }
 
 template <int B, typename TV, int W>
-void launch_solves(const bilu_pattern* p, int chunk, int nchunks, size_t smem, const TV* L, const TV* Dinv,
+void launch_solves(const bilu_pattern* p, int chunk, int nchunks, const TV* L, const TV* Dinv,
                    const TV* U, const double* r, double* y, double* x, int32_t* header, const TrisolveConfig& cfg,
                    int32_t* stop, void* stream) {
   cudaStream_t s = (cudaStream_t)stream;
   const int32_t n = p->n;
+  const size_t smem = tri_smem_bytes(chunk, B);
   {
-    const int grid = tri_grid<B, false, TV, W>(chunk, nchunks);
+    const int grid = tri_grid<B, false, TV, W>(smem, nchunks);
     ProfScope ps(BILU_PROF_LOWER, stream);
     tri_solve_kernel<B, false, TV, W><<<grid, W * 32, smem, s>>>(n, chunk, nchunks, p->d_lrp, p->d_lci, L,
-                                                                 nullptr, p->d_ord_l, p->d_tick_l, r, y, x,
+                                                                 nullptr, p->solve.d_ord_l, p->solve.d_tick_l, r, y, x,
                                                                  header, cfg.spin_ns, cfg.skip_row, stop);
   }
   {
-    const int grid = tri_grid<B, true, TV, W>(chunk, nchunks);
+    const int grid = tri_grid<B, true, TV, W>(smem, nchunks);
     ProfScope ps(BILU_PROF_UPPER, stream);
     tri_solve_kernel<B, true, TV, W><<<grid, W * 32, smem, s>>>(n, chunk, nchunks, p->d_urp, p->d_uci, U, Dinv,
-                                                                p->d_ord_u, p->d_tick_u, y, x, nullptr, header,
+                                                                p->solve.d_ord_u, p->solve.d_tick_u, y, x, nullptr, header,
                                                                 cfg.spin_ns, -1, stop);
   }
 }
@@ -314,8 +316,8 @@ int launch_apply_t(const bilu_pattern* p, int32_t b, const TV* f, const double* 
   if (n == 0) return 0;
   cudaStream_t s = (cudaStream_t)stream;
   const TrisolveConfig& cfg = trisolve_config();
-  const int chunk = p->sched_chunk;
-  if (chunk <= 0 || !p->d_sched) return (int)cudaErrorInvalidValue;
+  const int chunk = p->solve.chunk;
+  if (chunk <= 0 || !p->solve.upper || !p->solve.d_mem) return (int)cudaErrorInvalidValue;
   int32_t* header = reinterpret_cast<int32_t*>(work);
   double* y = reinterpret_cast<double*>(reinterpret_cast<char*>(work) + kHeaderBytes);
   const size_t bb = (size_t)b * b;
@@ -323,7 +325,6 @@ int launch_apply_t(const bilu_pattern* p, int32_t b, const TV* f, const double* 
   const TV* Dinv = f + (size_t)p->nnz_l() * bb;
   const TV* U = Dinv + (size_t)n * bb;
   const int nchunks = (n + chunk - 1) / chunk;
-  const size_t smem = tri_smem_bytes(chunk, b);
   const long long m = (long long)n * b;
   const int prep_blocks = (int)std::min<long long>((m + 255) / 256, (long long)sm_count() * 8);
   {
@@ -332,42 +333,49 @@ int launch_apply_t(const bilu_pattern* p, int32_t b, const TV* f, const double* 
   }
   BILU_DISPATCH_B(b, {
     if (cfg.warps == 16)
-      launch_solves<B, TV, 16>(p, chunk, nchunks, smem, L, Dinv, U, r, y, x, header, cfg, stop, stream);
+      launch_solves<B, TV, 16>(p, chunk, nchunks, L, Dinv, U, r, y, x, header, cfg, stop, stream);
     else if (cfg.warps == 4)
-      launch_solves<B, TV, 4>(p, chunk, nchunks, smem, L, Dinv, U, r, y, x, header, cfg, stop, stream);
+      launch_solves<B, TV, 4>(p, chunk, nchunks, L, Dinv, U, r, y, x, header, cfg, stop, stream);
     else
-      launch_solves<B, TV, 8>(p, chunk, nchunks, smem, L, Dinv, U, r, y, x, header, cfg, stop, stream);
+      launch_solves<B, TV, 8>(p, chunk, nchunks, L, Dinv, U, r, y, x, header, cfg, stop, stream);
   });
   return (int)cudaGetLastError();
 }
 
 }  // namespace
 
-int ensure_schedule(bilu_pattern* p, int32_t chunk) {
-  if (p->sched_chunk == chunk && (p->d_sched || p->n == 0)) return 0;
-  build_schedule(p, chunk);
-  if (p->d_sched) {
-    cudaFree(p->d_sched);
-    p->d_sched = nullptr;
-  }
+void free_schedule(bilu_chunk_schedule* s) {
+  if (s->d_mem) cudaFree(s->d_mem);
+  s->d_mem = nullptr;
+  s->d_ord_l = s->d_ord_u = s->d_tick_l = s->d_tick_u = nullptr;
+  s->chunk = 0;
+}
+
+int ensure_schedule(const bilu_pattern* p, bilu_chunk_schedule* s, int32_t chunk, bool upper) {
+  if (s->chunk == chunk && (s->upper || !upper) && (s->d_mem || p->n == 0)) return 0;
+  free_schedule(s);
+  build_schedule(p, chunk, upper, s);
   if (p->n == 0) return 0;
   const size_t one = align256(sizeof(int32_t) * (size_t)p->n);
-  const size_t tk = align256(sizeof(int32_t) * p->tick_l.size());
+  const size_t tk = align256(sizeof(int32_t) * s->tick_l.size());
+  const int parts = upper ? 2 : 1;
   void* mem = nullptr;
-  if (cudaMalloc(&mem, 2 * one + 2 * tk) != cudaSuccess) {
+  if (cudaMalloc(&mem, parts * (one + tk)) != cudaSuccess) {
     cudaGetLastError();
-    p->sched_chunk = 0;
+    s->chunk = 0;
     return (int)cudaErrorMemoryAllocation;
   }
-  p->d_sched = mem;
-  p->d_ord_l = (int32_t*)mem;
-  p->d_ord_u = (int32_t*)((char*)mem + one);
-  p->d_tick_l = (int32_t*)((char*)mem + 2 * one);
-  p->d_tick_u = (int32_t*)((char*)mem + 2 * one + tk);
-  cudaMemcpy(p->d_ord_l, p->ord_l.data(), sizeof(int32_t) * p->n, cudaMemcpyHostToDevice);
-  cudaMemcpy(p->d_ord_u, p->ord_u.data(), sizeof(int32_t) * p->n, cudaMemcpyHostToDevice);
-  cudaMemcpy(p->d_tick_l, p->tick_l.data(), sizeof(int32_t) * p->tick_l.size(), cudaMemcpyHostToDevice);
-  cudaMemcpy(p->d_tick_u, p->tick_u.data(), sizeof(int32_t) * p->tick_u.size(), cudaMemcpyHostToDevice);
+  s->d_mem = mem;
+  s->d_ord_l = (int32_t*)mem;
+  s->d_tick_l = (int32_t*)((char*)mem + one);
+  cudaMemcpy(s->d_ord_l, s->ord_l.data(), sizeof(int32_t) * p->n, cudaMemcpyHostToDevice);
+  cudaMemcpy(s->d_tick_l, s->tick_l.data(), sizeof(int32_t) * s->tick_l.size(), cudaMemcpyHostToDevice);
+  if (upper) {
+    s->d_ord_u = (int32_t*)((char*)mem + one + tk);
+    s->d_tick_u = (int32_t*)((char*)mem + 2 * one + tk);
+    cudaMemcpy(s->d_ord_u, s->ord_u.data(), sizeof(int32_t) * p->n, cudaMemcpyHostToDevice);
+    cudaMemcpy(s->d_tick_u, s->tick_u.data(), sizeof(int32_t) * s->tick_u.size(), cudaMemcpyHostToDevice);
+  }
   return (int)cudaGetLastError();
 }
 

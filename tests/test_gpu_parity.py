@@ -39,16 +39,23 @@ def _random_system(n, b, density, seed, symmetric=False):
     return BlockSystem(n=n, b=b, row_ptr=rp, col_idx=ci, vals=vals, rhs=rhs)
 
 
-def _check_factor_apply(B, S, k, chunks=(32, 1024)):
+def _check_factor_apply(B, S, k, chunks=(32, 1024), factor_chunks=(None,)):
     o = OracleRun(S.n, S.b, S.row_ptr, S.col_idx, S.vals, k)
     rp, ci, vals, rhs = device_system(S, DEV)
     P = B.bilu_symbolic(S.n, S.row_ptr, S.col_idx, k).upload()
-    F, info = B.bilu_factor(P, S.b, vals)
-    assert info.status == 0
-    Lg, Dg, Ug = (t.cpu().numpy() for t in B.factor_sections(P, S.b, F))
-    assert rel_maxerr(Lg, o.L()) <= TOL_FACTOR
-    assert rel_maxerr(Dg, o.Dinv) <= TOL_FACTOR
-    assert rel_maxerr(Ug, o.U()) <= TOL_FACTOR
+    old_f = B.bilu_get_factor_chunk()
+    try:
+        for fch in factor_chunks:
+            if fch is not None:
+                B.bilu_set_factor_chunk(fch)
+            F, info = B.bilu_factor(P, S.b, vals)
+            assert info.status == 0
+            Lg, Dg, Ug = (t.cpu().numpy() for t in B.factor_sections(P, S.b, F))
+            assert rel_maxerr(Lg, o.L()) <= TOL_FACTOR, fch
+            assert rel_maxerr(Dg, o.Dinv) <= TOL_FACTOR, fch
+            assert rel_maxerr(Ug, o.U()) <= TOL_FACTOR, fch
+    finally:
+        B.bilu_set_factor_chunk(old_f)
     xo = o.apply(S.rhs)
     old = B.bilu_get_trisolve_chunk()
     try:
@@ -78,20 +85,21 @@ def test_spmv(B, b, stencil):
 @pytest.mark.parametrize("k", [0, 1, 2])
 def test_factor_apply_grid(B, b, k):
     S = reservoir_system(13, 9, 6, b, sigma=1.0, accum=0.01, seed=10 * b + k)
-    _check_factor_apply(B, S, k, chunks=(1, 7, 32, 1024) if b in (1, 3, 8) else (32, 1024))
+    _check_factor_apply(B, S, k, chunks=(1, 7, 32, 1024) if b in (1, 3, 8) else (32, 1024),
+                        factor_chunks=(1, 7, 512, 1024) if b in (1, 3, 8) else (None,))
 
 
 @pytest.mark.parametrize("k", [0, 1, 3])
 def test_factor_apply_27pt(B, k):
     S = reservoir_system(9, 8, 7, 3, stencil=27, sigma=1.5, accum=1e-3, seed=5 + k)
-    _check_factor_apply(B, S, k, chunks=(1, 32, 100))
+    _check_factor_apply(B, S, k, chunks=(1, 32, 100), factor_chunks=(3, 100, 1024))
 
 
 @pytest.mark.parametrize("seed", range(4))
 @pytest.mark.parametrize("b", [2, 3, 7])
 def test_factor_apply_random_nonsymmetric(B, seed, b):
     S = _random_system(300 + 37 * seed, b, density=0.01 + 0.004 * seed, seed=50 + seed)
-    _check_factor_apply(B, S, seed % 3, chunks=(1, 16, 64))
+    _check_factor_apply(B, S, seed % 3, chunks=(1, 16, 64), factor_chunks=(1, 64, 512))
 
 
 def test_long_rows_full_fill(B):

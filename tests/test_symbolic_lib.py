@@ -105,3 +105,31 @@ def test_solve_schedule_is_a_valid_chunk_order(libbilu, rows, k):
                     dep = (j > i) if upper else (j < i)
                     if dep and lo <= j < hi:
                         assert where[j] < where[int(i)]
+
+
+@pytest.mark.parametrize("rows", [1, 7, 64, 256])
+@pytest.mark.parametrize("k", [0, 1, 2])
+def test_chunk_tickets_are_a_topological_order(libbilu, rows, k):
+    """The claim tickets list every chunk once, and every chunk a chunk depends
+    on (through any row) has a smaller ticket: no claimed chunk can wait on an
+    unclaimed one, whatever number of CTAs is resident."""
+    import paper_1703_01325_gb300.bilu as B
+    from paper_1703_01325_gb300.reservoir import reservoir_system
+    S = reservoir_system(13, 11, 6, 2, stencil=7 if k < 2 else 27)
+    P = B.bilu_symbolic(S.n, S.row_ptr, S.col_idx, k)
+    e = P.export()
+    rp, ci = e["row_ptr"], e["col_idx"]
+    n = S.n
+    nch = (n + rows - 1) // rows
+    _, _, tl, tu = P.schedule(rows, tickets=True)
+    for upper, tick in ((False, tl), (True, tu)):
+        assert sorted(tick.tolist()) == list(range(nch))
+        pos = np.empty(nch, np.int64)
+        pos[tick] = np.arange(nch)
+        chunk_of = (lambda j: (n - 1 - j) // rows) if upper else (lambda j: j // rows)
+        for i in range(n):
+            for t in range(rp[i], rp[i + 1]):
+                j = int(ci[t])
+                if (j > i) if upper else (j < i):
+                    a, b_ = chunk_of(i), chunk_of(j)
+                    assert a == b_ or pos[b_] < pos[a]
