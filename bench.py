@@ -42,6 +42,10 @@ if ROOT not in sys.path:
 METRIC = "Block-ILU(k) BiCGSTAB ms to 1e-8 resid; trisolve/SpMV GB/s; FP32-prec vs FP64"
 WORKLOAD = "grid128x128x64_7pt_b3"
 FP64_PEAK_TFLOPS = 1.196  # measured FP64 FMA rate of this GB300 (FMA = 2 flops)
+# DRAM bytes (read + write) per launch of a kernel, from one ncu capture of the
+# kernel as it stands (profiles/ holds the summary and the command); keyed by
+# (workload, k, kernel).  Empty entries report null.
+NCU_TRAFFIC = {}
 
 
 def parse():
@@ -52,11 +56,15 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--k", type=int, default=1)
+    ap.add_argument("--b", type=int, default=0, help="block size for workloads without one (default 3)")
     ap.add_argument("--tol", type=float, default=1e-8)
     ap.add_argument("--maxit", type=int, default=100)
     ap.add_argument("--chunk", type=int, default=0, help="trisolve rows per warp (0 = library default)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-precision", action="store_true", help="skip the FP32-preconditioner comparison")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="time the step only (no small-case, FP32-kernel or precision sections)")
     return ap.parse_args()
 
 
@@ -72,6 +80,8 @@ def peaks():
 def system(args):
     from paper_1703_01325_gb300.reservoir import WORKLOADS, reservoir_system
     cfg = dict(WORKLOADS[args.workload])
+    if "b" not in cfg or args.b:
+        cfg["b"] = args.b or cfg.get("b", 3)
     return reservoir_system(**cfg), cfg
 
 
@@ -233,6 +243,89 @@ def ms_to_tol_small(B, dev, stream, reps=5):
             "iters": info.iters, "true_relres": info.true_relres, "status": info.status}
 
 
+def precision_compare(B, dev, stream, cases=((2, 1), (4, 1)), tol=1e-8):
+    """FP32-stored preconditioner and FP32 SpMV inside FP64 iterative
+    refinement (bilu_factor_f32 + bicgstab_solve_mixed) against the plain
+    FP64 solve (bilu_factor + bicgstab_solve), both from x0 = 0 to a true
+    relative residual of `tol`, on the 96 x 96 x 48 7-point workload at block
+    sizes b and fill levels k.  Times include the factorization.  The mixed
+    solution's distance to the FP64 one (which the parity tests hold to the
+    CPU oracle) is reported as its error."""
+    import torch
+    from paper_1703_01325_gb300.reservoir import WORKLOADS, reservoir_system
+    out = []
+    for b, k in cases:
+        S = reservoir_system(b=b, **WORKLOADS["grid96x96x48_7pt"])
+        P = B.bilu_symbolic(S.n, S.row_ptr, S.col_idx, k).upload()
+        rp, ci = torch.from_numpy(S.row_ptr).to(dev), torch.from_numpy(S.col_idx).to(dev)
+        vals, rhs = torch.from_numpy(S.vals.reshape(-1)).to(dev), torch.from_numpy(S.rhs).to(dev)
+        A = (S.n, b, rp, ci, vals)
+        F = B.new_factors(P, b, dev)
+        F32 = torch.empty(max(P.factor_bytes_f32(b) // 4, 1), dtype=torch.float32, device=dev)
+        fw = B.workspace(P.factor_workspace_bytes(b), dev)
+        sw = B.workspace(P.bicgstab_workspace_bytes(b), dev)
+        mw = B.workspace(P.bicgstab_mixed_workspace_bytes(b), dev)
+        vals32 = B.bilu_convert_f32(vals)
+        x64, x32 = torch.zeros_like(rhs), torch.zeros_like(rhs)
+
+        def fp64():
+            B.bilu_factor(P, b, vals, F, fw)
+            x64.zero_()
+            return B.bicgstab_solve(P, A, F, rhs, x=x64, tol=tol, maxit=5000, work=sw)[1]
+
+        def mixed():
+            B.bilu_convert_f32(vals, vals32)
+            B.bilu_factor_f32(P, b, vals, F32, fw)
+            x32.zero_()
+            return B.bicgstab_solve_mixed(P, A, vals32, F32, rhs, x=x32, tol=tol, maxit=5000, inner_tol=1e-3,
+                                          inner_maxit=300, work=mw)[1]
+
+        row = {"workload": "grid96x96x48_7pt", "b": b, "k": k}
+        for name, fn in (("fp64", fp64), ("mixed", mixed)):
+            fn()  # warm-up
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            si = fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            row[name] = {"ms": round(e0.elapsed_time(e1), 2), "iters": si.iters, "true_relres": si.true_relres,
+                         "status": si.status}
+        row["mixed_x_rel_err_vs_fp64"] = float((x32 - x64).norm() / x64.norm())
+        row["mixed_speedup"] = round(row["fp64"]["ms"] / row["mixed"]["ms"], 3)
+        out.append(row)
+        P.close()
+    return out
+
+
+def fp32_kernel_rates(B, S, P, F, vals, rhs, rp, ci, dev, stream, reps=10):
+    """FP32-stored apply and FP32 SpMV on the main workload: mean CUDA-event
+    time and algorithmic GB/s (4-byte values)."""
+    import torch
+    info = P.info
+    b = S.b
+    ab = algorithmic_bytes(S.n, b, S.nnzb, info.nnz_l, info.nnz_u, v=4)
+    F32 = B.bilu_convert_f32(F)
+    V32 = B.bilu_convert_f32(vals)
+    aw = B.workspace(P.apply_workspace_bytes(b), dev)
+    x, y = torch.empty_like(rhs), torch.empty_like(rhs)
+    res = {}
+    for name, fn, by in (("apply_f32", lambda: B.bilu_apply_f32(P, b, F32, rhs, x, aw), ab["apply"]),
+                         ("spmv_f32", lambda: B.bsr_spmv_f32(S.n, b, rp, ci, V32, rhs, y), ab["spmv"])):
+        for _ in range(3):
+            fn()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        res[name] = {"avg_us": round(ms * 1e3, 1), "gbs": round(by / (ms * 1e-3) / 1e9, 1)}
+    return res
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -325,8 +418,10 @@ def main():
     roof = None
     if top:
         ach = kern[top]["gbs"]
+        traffic = NCU_TRAFFIC.get((args.workload, args.k, top))
         roof = {"kernel": top, "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
-                "frac": round(ach / hbm, 3), "traffic": None, "peak_source": peak_src}
+                "frac": round(ach / hbm, 3), "traffic": traffic, "peak_source": peak_src,
+                "algorithmic_bytes": ab[top]}
 
     # end to end through the public API: pinned host A values and rhs in, x out
     e2e = None
@@ -358,9 +453,12 @@ def main():
                "h2d_bytes_per_step": int(h_vals.numel() * 8 + h_rhs.numel() * 8),
                "d2h_bytes_per_step": int(h_x.numel() * 8)}
 
-    small = None
-    if rank == 0 and args.workload == WORKLOAD:
+    small = prec = f32 = None
+    if rank == 0 and args.workload == WORKLOAD and not args.no_extras:
         small = ms_to_tol_small(B, dev, stream)
+        f32 = fp32_kernel_rates(B, S, P, F, vals, rhs, rp, ci, dev, stream)
+        if not args.no_precision:
+            prec = precision_compare(B, dev, stream)
     if rank != 0:
         if dist:
             dist.destroy_process_group()
@@ -386,6 +484,7 @@ def main():
         "factor_ms": round(factor_ms / args.steps, 3), "symbolic_ms": round(symbolic_ms, 1),
         "per_iteration_ms": round((ms - factor_ms / args.steps) / max(gpu_iters, 1), 4),
         "ms_to_tol_small": small,
+        "fp32_prec_vs_fp64": prec, "fp32_kernels": f32,
         "kernels": kern, "roofline": roof, "e2e": e2e, "cpu_baseline": cpu,
         "gpu_launches": int(launches), "clocks": clocks.summary(),
         "fp64_alu": {"peak_tflops": FP64_PEAK_TFLOPS,

@@ -115,6 +115,12 @@ class Pattern:
     def bicgstab_workspace_bytes(self, b: int) -> int:
         return int(L.load().bicgstab_workspace_bytes(self.handle, b))
 
+    def bicgstab_mixed_workspace_bytes(self, b: int) -> int:
+        return int(L.load().bicgstab_mixed_workspace_bytes(self.handle, b))
+
+    def factor_bytes_f32(self, b: int) -> int:
+        return int(L.load().bilu_factor_bytes_f32(self.handle, b))
+
     def close(self):
         if self._h is not None:
             L.load().bilu_destroy_pattern(self._h)
