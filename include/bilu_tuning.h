@@ -34,18 +34,26 @@ int32_t bilu_get_factor_chunk(void);
  * operands ahead of its dependencies. */
 int bilu_set_trisolve_warps(int32_t warps);
 
-/* Host copy of the schedule the sync-free solves and the factorization use
- * for `rows` rows per chunk (the same one bilu_apply builds).
- *   ord_lower / ord_upper (n entries each): chunk c occupies positions
- *     [c*rows, c*rows + len) -- chunks of ascending rows for L, of descending
- *     rows starting from row n - 1 for U'; inside a chunk, rows are listed by
- *     their dependency level within the chunk.
- *   tick_lower / tick_upper (ceil(n / rows) entries each, may be NULL): the
- *     chunk each claim ticket hands out, a topological order of the chunk
- *     dependency graph.
- * Outputs are caller-allocated.  Host only. */
-int bilu_schedule_export(const bilu_pattern* p, int32_t rows, int32_t* ord_lower, int32_t* ord_upper,
-                         int32_t* tick_lower, int32_t* tick_upper);
+/* Host copy of the schedule the sync-free solves use for a target of `rows`
+ * rows per chunk (the same one bilu_apply builds; the factorization builds
+ * one the same way for its own target).  Rows are cut into *nchunks chunks
+ * of consecutive rows, chunk c = rows [bounds[c], bounds[c+1]); cuts fall
+ * where a row neither depends on its predecessor (L) nor is depended on by
+ * it (U'), the one nearest the target within [rows/2, 2*rows] (at most 1024
+ * rows), else at the target.
+ *   bounds (n + 1 entries capacity): the cut rows, bounds[0] = 0,
+ *     bounds[*nchunks] = n.
+ *   ord_lower / ord_upper (n entries): the rows of each chunk, at the
+ *     positions of the chunk's rows, listed by dependency level within the
+ *     chunk (ascending rows break ties for L, descending rows for U').
+ *   tick_lower / tick_upper (n entries capacity): the chunk each claim ticket
+ *     hands out, a topological order of the chunk dependency graph.  The
+ *     lower solve numbers chunks c = 0.. in ascending rows, the upper solve in
+ *     descending rows (its chunk c is chunk nchunks - 1 - c above).
+ * nchunks is required; any other output may be NULL.  Caller-allocated, host
+ * only. */
+int bilu_schedule_export(const bilu_pattern* p, int32_t rows, int32_t* nchunks, int32_t* bounds,
+                         int32_t* ord_lower, int32_t* ord_upper, int32_t* tick_lower, int32_t* tick_upper);
 
 /* Time limit of every bounded dependency wait in the factorization and the
  * triangular solves, in nanoseconds (default 2e9).  >= 1000, else

@@ -83,7 +83,7 @@ SIGNATURES = {
     "bilu_profile_enable": (C.c_int, [C.c_int32]),
     "bilu_profile_read": (C.c_int, [C.c_int32, C.POINTER(C.c_int64), C.POINTER(C.c_double)]),
     "bilu_launch_count": (C.c_int64, []),
-    "bilu_schedule_export": (C.c_int, [_vp, C.c_int32, _i32p, _i32p, _i32p, _i32p]),
+    "bilu_schedule_export": (C.c_int, [_vp, C.c_int32, _i32p, _i32p, _i32p, _i32p, _i32p, _i32p]),
 }
 
 PROF_KERNELS = ["spmv", "apply_prep", "lower_solve", "upper_solve", "backfill", "factor",

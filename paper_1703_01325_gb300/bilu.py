@@ -87,21 +87,23 @@ class Pattern:
         self.uploaded = True
         return self
 
-    def schedule(self, rows: int, tickets: bool = False):
-        """The chunk-local row orders of the sync-free solves, and with
-        ``tickets`` the chunk claim orders too (bilu_schedule_export)."""
+    def schedule(self, rows: int) -> dict:
+        """The sync-free solve schedule for a target of `rows` rows per chunk
+        (bilu_schedule_export): chunk bounds, chunk-local row orders and the
+        chunk claim orders of both solves."""
         n = self.info.n
-        nch = (n + rows - 1) // rows
+        nch = C.c_int32(0)
+        bounds = np.zeros(n + 1, np.int32)
         lo = np.zeros(max(n, 1), np.int32)
         up = np.zeros(max(n, 1), np.int32)
-        tl = np.zeros(max(nch, 1), np.int32)
-        tu = np.zeros(max(nch, 1), np.int32)
+        tl = np.zeros(max(n, 1), np.int32)
+        tu = np.zeros(max(n, 1), np.int32)
         p = lambda a: a.ctypes.data_as(C.POINTER(C.c_int32))
-        _check(L.load().bilu_schedule_export(self.handle, rows, p(lo), p(up), p(tl), p(tu)),
-               "bilu_schedule_export")
-        if tickets:
-            return lo[:n], up[:n], tl[:nch], tu[:nch]
-        return lo[:n], up[:n]
+        _check(L.load().bilu_schedule_export(self.handle, rows, C.byref(nch), p(bounds), p(lo), p(up), p(tl),
+                                             p(tu)), "bilu_schedule_export")
+        m = nch.value
+        return {"bounds": bounds[:m + 1], "ord_lower": lo[:n], "ord_upper": up[:n], "tick_lower": tl[:m],
+                "tick_upper": tu[:m]}
 
     def factor_bytes(self, b: int) -> int:
         return int(L.load().bilu_factor_bytes(self.handle, b))

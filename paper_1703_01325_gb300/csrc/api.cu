@@ -361,16 +361,23 @@ extern "C" int bilu_test_withhold_row(int32_t row) {
   return BILU_OK;
 }
 
-extern "C" int bilu_schedule_export(const bilu_pattern* p, int32_t rows, int32_t* ord_lower,
-                                    int32_t* ord_upper, int32_t* tick_lower, int32_t* tick_upper) {
-  if (!p || rows < 1 || rows > 1024 || (p->n > 0 && (!ord_lower || !ord_upper))) return BILU_ERR_ARG;
+extern "C" int bilu_schedule_export(const bilu_pattern* p, int32_t rows, int32_t* nchunks, int32_t* bounds,
+                                    int32_t* ord_lower, int32_t* ord_upper, int32_t* tick_lower,
+                                    int32_t* tick_upper) {
+  if (!p || !nchunks || rows < 1 || rows > 1024) return BILU_ERR_ARG;
   bilu_chunk_schedule tmp;
   build_schedule(p, rows, true, &tmp);
-  if (p->n > 0) {
-    std::memcpy(ord_lower, tmp.ord_l.data(), sizeof(int32_t) * (size_t)p->n);
-    std::memcpy(ord_upper, tmp.ord_u.data(), sizeof(int32_t) * (size_t)p->n);
-    if (tick_lower) std::memcpy(tick_lower, tmp.tick_l.data(), sizeof(int32_t) * tmp.tick_l.size());
-    if (tick_upper) std::memcpy(tick_upper, tmp.tick_u.data(), sizeof(int32_t) * tmp.tick_u.size());
+  *nchunks = tmp.nchunks;
+  const size_t n = (size_t)p->n;
+  auto put = [](int32_t* dst, const std::vector<int32_t>& v) {
+    if (dst && !v.empty()) std::memcpy(dst, v.data(), sizeof(int32_t) * v.size());
+  };
+  put(bounds, tmp.bnd);
+  if (n > 0) {
+    put(ord_lower, tmp.ord_l);
+    put(ord_upper, tmp.ord_u);
+    put(tick_lower, tmp.tick_l);
+    put(tick_upper, tmp.tick_u);
   }
   return BILU_OK;
 }

@@ -10,16 +10,21 @@
 #include "../../include/bilu.h"
 #include "../../include/bilu_tuning.h"
 
-// Sync-free schedule for one chunk size (symbolic.cpp builds it, trisolve.cu
-// uploads it): rows cut into chunks of `chunk` consecutive rows (ascending
-// chunks for L, descending for U'); ord_l / ord_u list each chunk's rows by
-// local dependency level; tick_l / tick_u give the chunk each claim ticket
-// hands out (a topological order of the chunk dependency graph).
+// Sync-free schedule for one target chunk size (symbolic.cpp builds it,
+// trisolve.cu uploads it): rows cut into chunks of consecutive rows, chunk c
+// = rows [bnd[c], bnd[c+1]) (walked in ascending chunk order for L, descending
+// for U'); ord_l / ord_u list each chunk's rows by local dependency level at
+// the positions of the chunk's rows; tick_l / tick_u give the chunk each
+// claim ticket hands out (a topological order of the chunk dependency graph;
+// upper chunk c is lower chunk nchunks-1-c).
 struct bilu_chunk_schedule {
-  int32_t chunk = 0;
-  bool upper = false;  // ord_u / tick_u built too
-  std::vector<int32_t> ord_l, ord_u, tick_l, tick_u;
+  int32_t chunk = 0;    // target rows per chunk the schedule was built for
+  bool upper = false;   // ord_u / tick_u built too
+  int32_t nchunks = 0;
+  int32_t max_len = 0;  // rows of the longest chunk
+  std::vector<int32_t> bnd, ord_l, ord_u, tick_l, tick_u;
   void* d_mem = nullptr;
+  int32_t* d_bnd = nullptr;
   int32_t* d_ord_l = nullptr;
   int32_t* d_ord_u = nullptr;
   int32_t* d_tick_l = nullptr;

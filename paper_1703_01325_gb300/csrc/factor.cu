@@ -68,7 +68,8 @@ size_t factor_smem_bytes(int chunk) {
 
 template <int B, typename TV>
 __global__ void __launch_bounds__(FactorCap<B>::W * 32) factor_kernel(
-    int32_t n, int32_t chunk, int32_t nchunks, const int32_t* __restrict__ ord, const int32_t* __restrict__ tick,
+    int32_t n, int32_t chunk, int32_t nchunks, const int32_t* __restrict__ bnd, const int32_t* __restrict__ ord,
+    const int32_t* __restrict__ tick,
     const int32_t* __restrict__ lrp, const int32_t* __restrict__ lci,
     const int32_t* __restrict__ urp, const int32_t* __restrict__ uci, TV* f, long long nnz_l,
     int32_t* header, int32_t* done, long long spin_ns) {
@@ -104,8 +105,7 @@ __global__ void __launch_bounds__(FactorCap<B>::W * 32) factor_kernel(
     __syncthreads();
     const int c = s_c;
     if (c >= nchunks) return;
-    const int lo = c * chunk;
-    const int hi = min(lo + chunk, n);
+    const int lo = bnd[c], hi = bnd[c + 1];  // at most `chunk` rows
     const int len = hi - lo;
     for (int q = tid; q < len; q += blockDim.x) s_i[q] = ord[lo + q];
     __syncthreads();
@@ -310,43 +310,36 @@ __global__ void __launch_bounds__(FactorCap<B>::W * 32) factor_kernel(
   }
 }
 
-// Eq. 5: U'_ij = D_i^{-1} U_ij, one warp per block row.
+// Eq. 5: U'_ij = D_i^{-1} U_ij, one warp per block row; lane q of the row's
+// (block, column) pairs reads one column of U_ij, forms that column of
+// D_i^{-1} U_ij (b x b FMAs) and writes it back in place.  Columns are
+// independent, so no lane waits on another.
 template <int B, typename TV>
-__global__ void __launch_bounds__(128) scale_upper_kernel(int32_t n, const int32_t* __restrict__ urp,
+__global__ void __launch_bounds__(256) scale_upper_kernel(int32_t n, const int32_t* __restrict__ urp,
                                                           const TV* __restrict__ dinv,
                                                           TV* __restrict__ u) {
   constexpr int BB = B * B;
-  constexpr int H = (BB + 31) / 32;
-  __shared__ TV s_d[4][BB];
-  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  TV* d = s_d[wib];
-  const long long nw = (long long)gridDim.x * 4;
-  for (long long i = (long long)blockIdx.x * 4 + wib; i < n; i += nw) {
-    for (int e = lane; e < BB; e += 32) d[e] = dinv[(size_t)i * BB + e];
-    __syncwarp();
-    for (int t = urp[i]; t < urp[i + 1]; ++t) {
-      TV* blk = u + (size_t)t * BB;
-      TV nv[H];
+  const int lane = threadIdx.x & 31;
+  const long long nw = (long long)gridDim.x * (blockDim.x >> 5);
+  for (long long i = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < n; i += nw) {
+    const int ub = urp[i], cnt = (urp[i + 1] - ub) * B;
+    if (cnt == 0) continue;
+    TV d[BB];  // D_i^{-1}, column-major
 #pragma unroll
-      for (int h = 0; h < H; ++h) {
-        const int e = lane + 32 * h;
-        if (e < BB) {
-          const int r = e % B, c = e / B;
-          TV s = TV(0);
+    for (int e = 0; e < BB; ++e) d[e] = __ldg(dinv + (size_t)i * BB + e);
+    for (int q = lane; q < cnt; q += 32) {
+      TV* col = u + ((size_t)ub + q / B) * BB + (q % B) * B;
+      TV x[B];
 #pragma unroll
-          for (int m = 0; m < B; ++m) s = fma(d[m * B + r], blk[c * B + m], s);
-          nv[h] = s;
-        }
+      for (int m = 0; m < B; ++m) x[m] = col[m];
+#pragma unroll
+      for (int r = 0; r < B; ++r) {
+        TV acc = TV(0);
+#pragma unroll
+        for (int m = 0; m < B; ++m) acc = fma(d[m * B + r], x[m], acc);
+        col[r] = acc;
       }
-      __syncwarp();
-#pragma unroll
-      for (int h = 0; h < H; ++h) {
-        const int e = lane + 32 * h;
-        if (e < BB) blk[e] = nv[h];
-      }
-      __syncwarp();
     }
-    __syncwarp();
   }
 }
 
@@ -378,9 +371,9 @@ int launch_factor_t(const bilu_pattern* p, int32_t b, TV* f, int32_t* header, in
     factor_init_kernel<<<std::max(1, std::min((n + 255) / 256, sms * 4)), 256, 0, s>>>(header, done, n);
   }
   if (n == 0) return (int)cudaGetLastError();
-  const int chunk = p->fact.chunk;
-  if (chunk <= 0 || !p->fact.d_mem) return (int)cudaErrorInvalidValue;
-  const int nchunks = (n + chunk - 1) / chunk;
+  if (p->fact.chunk <= 0 || !p->fact.d_mem) return (int)cudaErrorInvalidValue;
+  const int chunk = p->fact.max_len;  // shared-memory rows per CTA
+  const int nchunks = p->fact.nchunks;
   const long long spin = trisolve_config().spin_ns;
   BILU_DISPATCH_B(b, {
     const size_t smem = factor_smem_bytes<B, TV>(chunk);
@@ -395,7 +388,7 @@ int launch_factor_t(const bilu_pattern* p, int32_t b, TV* f, int32_t* header, in
     }
     const int grid = std::max(1, std::min(nchunks, per_sm * sms));
     ProfScope ps(BILU_PROF_FACTOR, stream);
-    factor_kernel<B, TV><<<grid, FactorCap<B>::W * 32, smem, s>>>(n, chunk, nchunks, p->fact.d_ord_l, p->fact.d_tick_l, p->d_lrp, p->d_lci,
+    factor_kernel<B, TV><<<grid, FactorCap<B>::W * 32, smem, s>>>(n, chunk, nchunks, p->fact.d_bnd, p->fact.d_ord_l, p->fact.d_tick_l, p->d_lrp, p->d_lci,
                                                             p->d_urp, p->d_uci, f, p->nnz_l(), header, done,
                                                             spin);
   });
@@ -409,10 +402,10 @@ int launch_scale_upper_t(const bilu_pattern* p, int32_t b, TV* f, void* stream) 
   const size_t bb = (size_t)b * b;
   const TV* dinv = f + (size_t)p->nnz_l() * bb;
   TV* u = f + ((size_t)p->nnz_l() + n) * bb;
-  const int grid = std::max(1, std::min((n + 3) / 4, device_sms() * 16));
+  const int grid = std::max(1, std::min((n + 7) / 8, device_sms() * 8));
   BILU_DISPATCH_B(b, {
     ProfScope ps(BILU_PROF_SCALE_UPPER, stream);
-    scale_upper_kernel<B, TV><<<grid, 128, 0, (cudaStream_t)stream>>>(n, p->d_urp, dinv, u);
+    scale_upper_kernel<B, TV><<<grid, 256, 0, (cudaStream_t)stream>>>(n, p->d_urp, dinv, u);
   });
   return (int)cudaGetLastError();
 }

@@ -16,6 +16,7 @@
 
 #include <algorithm>
 #include <climits>
+#include <cstdlib>
 #include <cstring>
 #include <functional>
 #include <new>
@@ -212,13 +213,29 @@ extern "C" int bilu_pattern_export(const bilu_pattern* p, int32_t* row_ptr, int3
 
 namespace bilu {
 
-// Chunk-local dependency order of the sync-free triangular solves.  Rows are
-// cut into chunks of `chunk` consecutive rows; the lower solve takes chunks in
-// ascending order, the upper solve in descending order.  Inside a chunk, the
-// local level of a row is 1 + the largest local level of the rows of the same
-// chunk it depends on (0 if none), i.e. Eq. 4 restricted to the chunk; rows
-// are listed by (local level, row) for L and (local level, descending row) for
-// U'.  Chunk c occupies positions [c*chunk, c*chunk + len) of ord_l / ord_u.
+// Schedule of the sync-free triangular solves and factorization.
+//
+// Chunks.  Rows are cut into chunks of consecutive rows, about `target` rows
+// each; the lower solve and the factorization walk chunks in ascending order,
+// the upper solve in descending order.  The gap of a row r is the distance to
+// its nearest dependency below it, r - max{j < r in L(r)} (and, for U',
+// min{j > r-1 in U(r-1)} - (r-1); the smaller of the two counts).  A cut is
+// placed before the row of largest gap > 1 in [target/2, 2*target] rows (at
+// most 1024) from the chunk's start, the one nearest to `target` among equal
+// gaps; else at `target`.  In a natural grid ordering the rows of gap > 1
+// start grid lines and the largest gaps start planes, so chunks hold whole
+// lines and never straddle a plane: the chain along a line never crosses a
+// chunk boundary (a chunk cut inside a line would wait for the previous
+// chunk's last row before its first row could start), and no chunk mixes the
+// end of one plane with the start of the next (whose rows become ready a
+// whole plane apart, holding the chunk's CTA in between).
+//
+// Order inside a chunk.  The local level of a row is 1 + the largest local
+// level of the rows of the same chunk it depends on (0 if none), i.e. Eq. 4
+// restricted to the chunk; rows are listed by (local level, row) for L and
+// (local level, descending row) for U'.  Chunk [lo, hi) occupies positions
+// [lo, hi) of ord_l and of ord_u.
+//
 // Tickets hand chunks out in a topological order of the chunk dependency
 // graph (a chunk depends on every other chunk holding a row one of its rows
 // depends on), so a chunk only ever waits on chunks of smaller tickets.  The
@@ -227,18 +244,53 @@ namespace bilu {
 // smallest Eq. 4 level (then the smaller chunk index).  The Eq. 4 level of a
 // row is where it sits on the longest dependency chain, i.e. roughly when it
 // can start, so chunks are claimed in about the order they can run and few
-// resident CTAs sit on chunks that cannot start yet.
-void build_schedule(const bilu_pattern* p, int32_t chunk, bool upper, bilu_chunk_schedule* s) {
+// resident CTAs sit on chunks that cannot start yet.  Chunk numbers: lower
+// chunk c is bnd[c]..bnd[c+1]; upper chunk c is lower chunk nchunks-1-c.
+void build_schedule(const bilu_pattern* p, int32_t target, bool upper, bilu_chunk_schedule* s) {
   const int32_t n = p->n;
+  // chunk boundaries
+  auto gap = [&](int32_t r) -> int64_t {  // 0 < r < n
+    int64_t g = p->lrp[r + 1] > p->lrp[r] ? (int64_t)r - p->lci[p->lrp[r + 1] - 1] : INT64_MAX;
+    if (upper && p->urp[r] > p->urp[r - 1]) g = std::min<int64_t>(g, (int64_t)p->uci[p->urp[r - 1]] - (r - 1));
+    return g;
+  };
+  s->bnd.clear();
+  s->bnd.push_back(0);
+  int32_t max_len = 0;
+  for (int32_t lo = 0; lo < n;) {
+    int32_t hi = (int32_t)std::min<int64_t>(n, (int64_t)lo + target);
+    if (hi < n) {
+      const int32_t a = lo + std::max(1, target / 2);
+      const int32_t z = (int32_t)std::min<int64_t>({(int64_t)n - 1, (int64_t)lo + 2LL * target, (int64_t)lo + 1024});
+      int32_t best = -1;
+      int64_t best_gap = 1;
+      for (int32_t r = a; r <= z; ++r) {
+        const int64_t g = gap(r);
+        if (g <= 1 || g < best_gap) continue;  // gap 1: r depends on r - 1
+        if (g > best_gap || std::abs(r - (lo + target)) < std::abs(best - (lo + target))) {
+          best = r;
+          best_gap = g;
+        }
+      }
+      if (best > lo) hi = best;
+    }
+    max_len = std::max(max_len, hi - lo);
+    s->bnd.push_back(hi);
+    lo = hi;
+  }
+  const int32_t nchunks = (int32_t)s->bnd.size() - 1;
+  s->nchunks = nchunks;
+  s->max_len = max_len;
+  std::vector<int32_t> chunk_of((size_t)n);
+  for (int32_t c = 0; c < nchunks; ++c)
+    for (int32_t i = s->bnd[c]; i < s->bnd[c + 1]; ++i) chunk_of[i] = c;
+
   s->ord_l.assign((size_t)n, 0);
   s->ord_u.assign(upper ? (size_t)n : 0, 0);
-
-  std::vector<int32_t> loc((size_t)std::max(chunk, 1), 0);
+  std::vector<int32_t> loc((size_t)std::max(max_len, 1), 0);
   std::vector<std::pair<int32_t, int32_t>> key;
-  const int32_t nchunks = (n + chunk - 1) / chunk;
   for (int32_t c = 0; c < nchunks; ++c) {
-    // lower: rows [lo, hi)
-    int32_t lo = c * chunk, hi = std::min(n, lo + chunk);
+    const int32_t lo = s->bnd[c], hi = s->bnd[c + 1];
     key.clear();
     for (int32_t i = lo; i < hi; ++i) {
       int32_t l = 0;
@@ -248,11 +300,8 @@ void build_schedule(const bilu_pattern* p, int32_t chunk, bool upper, bilu_chunk
       key.emplace_back(l, i);
     }
     std::sort(key.begin(), key.end());
-    for (size_t q = 0; q < key.size(); ++q) s->ord_l[(size_t)c * chunk + q] = key[q].second;
+    for (size_t q = 0; q < key.size(); ++q) s->ord_l[(size_t)lo + q] = key[q].second;
     if (!upper) continue;
-    // upper: rows [lo, hi) with hi = n - c*chunk
-    hi = n - c * chunk;
-    lo = std::max(0, hi - chunk);
     key.clear();
     for (int32_t i = hi - 1; i >= lo; --i) {
       int32_t l = 0;
@@ -262,7 +311,7 @@ void build_schedule(const bilu_pattern* p, int32_t chunk, bool upper, bilu_chunk
       key.emplace_back(l, -i);
     }
     std::sort(key.begin(), key.end());
-    for (size_t q = 0; q < key.size(); ++q) s->ord_u[(size_t)c * chunk + q] = -key[q].second;
+    for (size_t q = 0; q < key.size(); ++q) s->ord_u[(size_t)lo + q] = -key[q].second;
   }
   // ticket orders (list scheduling over the chunk dependency graph)
   auto ticket_order = [&](bool up, std::vector<int32_t>& tick) {
@@ -270,18 +319,17 @@ void build_schedule(const bilu_pattern* p, int32_t chunk, bool upper, bilu_chunk
     const std::vector<int32_t>& civ = up ? p->uci : p->lci;
     const std::vector<int32_t>& lvl = up ? p->lvl_u : p->lvl_l;
     std::vector<int32_t> prio((size_t)nchunks, 0), indeg((size_t)nchunks, 0), seen((size_t)nchunks, -1);
-    std::vector<int32_t> epred, esucc;  // distinct edges pred -> succ
+    std::vector<int32_t> epred, esucc;  // distinct edges pred -> succ (solve-order chunk numbers)
     for (int32_t c = 0; c < nchunks; ++c) {
-      int32_t lo, hi;
-      if (!up) { lo = c * chunk; hi = std::min(n, lo + chunk); }
-      else { hi = n - c * chunk; lo = std::max(0, hi - chunk); }
+      const int32_t lc = up ? nchunks - 1 - c : c;  // the chunk's rows
+      const int32_t lo = s->bnd[lc], hi = s->bnd[lc + 1];
       int32_t pm = INT32_MAX;
       for (int32_t i = lo; i < hi; ++i) {
         pm = std::min(pm, lvl.empty() ? 0 : lvl[i]);
         for (int32_t t = rpv[i]; t < rpv[i + 1]; ++t) {
           const int32_t j = civ[t];
           if (j >= lo && j < hi) continue;
-          const int32_t cj = up ? (n - 1 - j) / chunk : j / chunk;
+          const int32_t cj = up ? nchunks - 1 - chunk_of[j] : chunk_of[j];
           if (seen[cj] == c) continue;
           seen[cj] = c;
           epred.push_back(cj);
@@ -314,12 +362,12 @@ void build_schedule(const bilu_pattern* p, int32_t chunk, bool upper, bilu_chunk
       for (int64_t e = off[c]; e < off[c + 1]; ++e)
         if (--indeg[succ[e]] == 0) ready.emplace(prio[succ[e]], succ[e]);
     }
-    // the chunk graph of a triangular pattern is acyclic: every chunk is listed
+    // a chunk depends only on chunks earlier in solve order: every chunk is listed
   };
   ticket_order(false, s->tick_l);
   if (upper) ticket_order(true, s->tick_u);
   else s->tick_u.clear();
-  s->chunk = chunk;
+  s->chunk = target;
   s->upper = upper;
 }
 

@@ -129,7 +129,7 @@ __device__ __forceinline__ void fetch_deps(RowPre<B, UPPER, TV>& p, const double
 
 template <int B, bool UPPER, typename TV, int kTriWarps>
 __global__ void __launch_bounds__(kTriWarps * 32) tri_solve_kernel(
-    int32_t n, int32_t chunk, int32_t nchunks, const int32_t* __restrict__ rp,
+    int32_t n, int32_t chunk, int32_t nchunks, const int32_t* __restrict__ bnd, const int32_t* __restrict__ rp,
     const int32_t* __restrict__ ci, const TV* __restrict__ vals, const TV* __restrict__ dinv,
     const int32_t* __restrict__ ord, const int32_t* __restrict__ tick, const double* rhs, double* out,
     double* pend_out, int32_t* header, long long spin_ns, int32_t skip_row, int32_t* stop) {
@@ -156,18 +156,12 @@ __global__ void __launch_bounds__(kTriWarps * 32) tri_solve_kernel(
     __syncthreads();
     const int c = s_c;
     if (c >= nchunks) return;
-    int lo, hi;
-    if (!UPPER) {
-      lo = c * chunk;
-      hi = min(lo + chunk, n);
-    } else {
-      hi = n - c * chunk;
-      lo = max(hi - chunk, 0);
-    }
+    // rows [lo, hi), at most `chunk` of them; upper chunk c is lower chunk nchunks-1-c
+    const int lc = UPPER ? nchunks - 1 - c : c;
+    const int lo = bnd[lc], hi = bnd[lc + 1];
     const int len = hi - lo;
-    const int base = c * chunk;
     for (int q = tid; q < len; q += blockDim.x) {
-      const int i = ord[base + q];
+      const int i = ord[lo + q];
       s_i[q] = i;
       s_beg[q] = rp[i];
       s_end[q] = rp[i + 1];
@@ -296,14 +290,14 @@ void launch_solves(const bilu_pattern* p, int chunk, int nchunks, const TV* L, c
   {
     const int grid = tri_grid<B, false, TV, W>(smem, nchunks);
     ProfScope ps(BILU_PROF_LOWER, stream);
-    tri_solve_kernel<B, false, TV, W><<<grid, W * 32, smem, s>>>(n, chunk, nchunks, p->d_lrp, p->d_lci, L,
+    tri_solve_kernel<B, false, TV, W><<<grid, W * 32, smem, s>>>(n, chunk, nchunks, p->solve.d_bnd, p->d_lrp, p->d_lci, L,
                                                                  nullptr, p->solve.d_ord_l, p->solve.d_tick_l, r, y, x,
                                                                  header, cfg.spin_ns, cfg.skip_row, stop);
   }
   {
     const int grid = tri_grid<B, true, TV, W>(smem, nchunks);
     ProfScope ps(BILU_PROF_UPPER, stream);
-    tri_solve_kernel<B, true, TV, W><<<grid, W * 32, smem, s>>>(n, chunk, nchunks, p->d_urp, p->d_uci, U, Dinv,
+    tri_solve_kernel<B, true, TV, W><<<grid, W * 32, smem, s>>>(n, chunk, nchunks, p->solve.d_bnd, p->d_urp, p->d_uci, U, Dinv,
                                                                 p->solve.d_ord_u, p->solve.d_tick_u, y, x, nullptr, header,
                                                                 cfg.spin_ns, -1, stop);
   }
@@ -316,15 +310,15 @@ int launch_apply_t(const bilu_pattern* p, int32_t b, const TV* f, const double* 
   if (n == 0) return 0;
   cudaStream_t s = (cudaStream_t)stream;
   const TrisolveConfig& cfg = trisolve_config();
-  const int chunk = p->solve.chunk;
-  if (chunk <= 0 || !p->solve.upper || !p->solve.d_mem) return (int)cudaErrorInvalidValue;
+  if (p->solve.chunk <= 0 || !p->solve.upper || !p->solve.d_mem) return (int)cudaErrorInvalidValue;
+  const int chunk = p->solve.max_len;  // shared-memory rows per CTA
+  const int nchunks = p->solve.nchunks;
   int32_t* header = reinterpret_cast<int32_t*>(work);
   double* y = reinterpret_cast<double*>(reinterpret_cast<char*>(work) + kHeaderBytes);
   const size_t bb = (size_t)b * b;
   const TV* L = f;
   const TV* Dinv = f + (size_t)p->nnz_l() * bb;
   const TV* U = Dinv + (size_t)n * bb;
-  const int nchunks = (n + chunk - 1) / chunk;
   const long long m = (long long)n * b;
   const int prep_blocks = (int)std::min<long long>((m + 255) / 256, (long long)sm_count() * 8);
   {
@@ -347,7 +341,7 @@ int launch_apply_t(const bilu_pattern* p, int32_t b, const TV* f, const double* 
 void free_schedule(bilu_chunk_schedule* s) {
   if (s->d_mem) cudaFree(s->d_mem);
   s->d_mem = nullptr;
-  s->d_ord_l = s->d_ord_u = s->d_tick_l = s->d_tick_u = nullptr;
+  s->d_bnd = s->d_ord_l = s->d_ord_u = s->d_tick_l = s->d_tick_u = nullptr;
   s->chunk = 0;
 }
 
@@ -357,22 +351,26 @@ int ensure_schedule(const bilu_pattern* p, bilu_chunk_schedule* s, int32_t chunk
   build_schedule(p, chunk, upper, s);
   if (p->n == 0) return 0;
   const size_t one = align256(sizeof(int32_t) * (size_t)p->n);
-  const size_t tk = align256(sizeof(int32_t) * s->tick_l.size());
+  const size_t tk = align256(sizeof(int32_t) * (size_t)s->nchunks);
+  const size_t bd = align256(sizeof(int32_t) * ((size_t)s->nchunks + 1));
   const int parts = upper ? 2 : 1;
   void* mem = nullptr;
-  if (cudaMalloc(&mem, parts * (one + tk)) != cudaSuccess) {
+  if (cudaMalloc(&mem, bd + parts * (one + tk)) != cudaSuccess) {
     cudaGetLastError();
     s->chunk = 0;
     return (int)cudaErrorMemoryAllocation;
   }
+  char* m = (char*)mem;
   s->d_mem = mem;
-  s->d_ord_l = (int32_t*)mem;
-  s->d_tick_l = (int32_t*)((char*)mem + one);
+  s->d_bnd = (int32_t*)m;
+  s->d_ord_l = (int32_t*)(m + bd);
+  s->d_tick_l = (int32_t*)(m + bd + one);
+  cudaMemcpy(s->d_bnd, s->bnd.data(), sizeof(int32_t) * s->bnd.size(), cudaMemcpyHostToDevice);
   cudaMemcpy(s->d_ord_l, s->ord_l.data(), sizeof(int32_t) * p->n, cudaMemcpyHostToDevice);
   cudaMemcpy(s->d_tick_l, s->tick_l.data(), sizeof(int32_t) * s->tick_l.size(), cudaMemcpyHostToDevice);
   if (upper) {
-    s->d_ord_u = (int32_t*)((char*)mem + one + tk);
-    s->d_tick_u = (int32_t*)((char*)mem + 2 * one + tk);
+    s->d_ord_u = (int32_t*)(m + bd + one + tk);
+    s->d_tick_u = (int32_t*)(m + bd + 2 * one + tk);
     cudaMemcpy(s->d_ord_u, s->ord_u.data(), sizeof(int32_t) * p->n, cudaMemcpyHostToDevice);
     cudaMemcpy(s->d_tick_u, s->tick_u.data(), sizeof(int32_t) * s->tick_u.size(), cudaMemcpyHostToDevice);
   }

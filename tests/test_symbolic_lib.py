@@ -74,29 +74,32 @@ def test_error_codes(libbilu):
     assert libbilu.bilu_status_string(L.BILU_ERR_TIMEOUT).decode().startswith("a bounded")
 
 
+def _chunk_ranges(sched):
+    bnd = sched["bounds"]
+    return [(int(bnd[c]), int(bnd[c + 1])) for c in range(len(bnd) - 1)]
+
+
 @pytest.mark.parametrize("rows", [1, 5, 64, 1024])
 @pytest.mark.parametrize("k", [0, 2])
 def test_solve_schedule_is_a_valid_chunk_order(libbilu, rows, k):
-    """Each chunk of the sync-free solves lists exactly its rows, and every
-    dependency of a row inside the same chunk comes earlier in the list."""
+    """The chunks partition the rows into consecutive ranges of at most 1024
+    rows; each chunk lists exactly its rows, and every dependency of a row
+    inside the same chunk comes earlier in the list."""
     import paper_1703_01325_gb300.bilu as B
     from paper_1703_01325_gb300.reservoir import reservoir_system
     S = reservoir_system(11, 9, 7, 2, stencil=7 if k else 27)
     P = B.bilu_symbolic(S.n, S.row_ptr, S.col_idx, k)
     e = P.export()
     rp, ci = e["row_ptr"], e["col_idx"]
-    ordl, ordu = P.schedule(rows)
+    sch = P.schedule(rows)
     n = S.n
-    nch = (n + rows - 1) // rows
-    for c in range(nch):
+    ranges = _chunk_ranges(sch)
+    assert ranges[0][0] == 0 and ranges[-1][1] == n
+    assert all(a < b_ <= a + 1024 for a, b_ in ranges)
+    assert all(ranges[c][1] == ranges[c + 1][0] for c in range(len(ranges) - 1))
+    for lo, hi in ranges:
         for upper in (False, True):
-            if not upper:
-                lo, hi = c * rows, min(n, (c + 1) * rows)
-                seq = ordl[c * rows:c * rows + hi - lo]
-            else:
-                hi = n - c * rows
-                lo = max(0, hi - rows)
-                seq = ordu[c * rows:c * rows + hi - lo]
+            seq = (sch["ord_upper"] if upper else sch["ord_lower"])[lo:hi]
             assert sorted(seq.tolist()) == list(range(lo, hi))
             where = {int(i): q for q, i in enumerate(seq)}
             for i in seq:
@@ -120,16 +123,52 @@ def test_chunk_tickets_are_a_topological_order(libbilu, rows, k):
     e = P.export()
     rp, ci = e["row_ptr"], e["col_idx"]
     n = S.n
-    nch = (n + rows - 1) // rows
-    _, _, tl, tu = P.schedule(rows, tickets=True)
-    for upper, tick in ((False, tl), (True, tu)):
+    sch = P.schedule(rows)
+    ranges = _chunk_ranges(sch)
+    nch = len(ranges)
+    chunk_of = np.empty(n, np.int64)
+    for c, (lo, hi) in enumerate(ranges):
+        chunk_of[lo:hi] = c
+    for upper, tick in ((False, sch["tick_lower"]), (True, sch["tick_upper"])):
         assert sorted(tick.tolist()) == list(range(nch))
         pos = np.empty(nch, np.int64)
         pos[tick] = np.arange(nch)
-        chunk_of = (lambda j: (n - 1 - j) // rows) if upper else (lambda j: j // rows)
+        num = (lambda j: nch - 1 - chunk_of[j]) if upper else (lambda j: chunk_of[j])
         for i in range(n):
             for t in range(rp[i], rp[i + 1]):
                 j = int(ci[t])
                 if (j > i) if upper else (j < i):
-                    a, b_ = chunk_of(i), chunk_of(j)
+                    a, b_ = num(i), num(j)
                     assert a == b_ or pos[b_] < pos[a]
+
+
+@pytest.mark.parametrize("nx,rows,want", [(96, 256, 288), (128, 256, 256), (160, 256, 320), (96, 512, 576),
+                                          (40, 100, 80)])
+@pytest.mark.parametrize("k", [0, 1])
+def test_chunks_hold_whole_grid_lines(libbilu, nx, rows, want, k):
+    """On a natural-order grid the cuts fall at line starts (rows that do not
+    depend on their predecessor), at the multiple of the line length nearest
+    the target (a tie goes to the shorter chunk), and at every plane start
+    (the largest dependency gap) that a chunk's window reaches, so no chunk
+    straddles two planes."""
+    import paper_1703_01325_gb300.bilu as B
+    ny, nz = 6, 4
+    rp, ci = grid_pattern(nx, ny, nz, 7)
+    n = nx * ny * nz
+    P = B.bilu_symbolic(n, rp, ci, k)
+    bnd = P.schedule(rows)["bounds"]
+    assert all(int(x) % nx == 0 for x in bnd)
+    assert int(bnd[1]) == want
+    assert set(range(0, n, nx * ny)) <= set(bnd.tolist())
+
+
+def test_chunks_without_line_structure_use_the_target(libbilu):
+    """A tridiagonal chain has no clean cut: every chunk has the target size."""
+    import paper_1703_01325_gb300.bilu as B
+    n = 1000
+    rows_ = [[j for j in (i - 1, i, i + 1) if 0 <= j < n] for i in range(n)]
+    rp = np.concatenate([[0], np.cumsum([len(r) for r in rows_])]).astype(np.int32)
+    ci = np.concatenate(rows_).astype(np.int32)
+    P = B.bilu_symbolic(n, rp, ci, 0)
+    bnd = P.schedule(64)["bounds"]
+    assert bnd.tolist() == list(range(0, n, 64)) + [n]
