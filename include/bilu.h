@@ -343,6 +343,51 @@ int bicgstab_solve_mixed(const bilu_pattern* p, const bilu_bsr* A, const float* 
                          int32_t maxit, double inner_tol, int32_t inner_maxit, void* d_work,
                          size_t work_bytes, void* stream, bilu_solve_info* info);
 
+/* ---- adjoint: A^T lambda = g with the transposed factors ----
+ *
+ * A loss L(x) through x = A^{-1} b has dL/db = lambda and dL/dA_IJ =
+ * -lambda_I x_J^T (on A's block pattern), where A^T lambda = dL/dx.  With
+ * M = L D U' (Eq. 5-6), M^T = U'^T D^T L^T: the preconditioner of the adjoint
+ * solve is the apply of Eq. 6 / Algorithm 7 on the transposed pattern P'^T
+ * (whose strictly lower part is U'^T and strictly upper part L^T) with every
+ * block transposed, so bilu_apply, bicgstab_solve and bsr_spmv serve the
+ * adjoint unchanged once the transposes below exist.
+ */
+
+/* The transposed pattern P'^T of p (host; library-owned handle, freed by
+ * bilu_destroy_pattern; upload it before use).  It serves bilu_apply,
+ * bicgstab_solve and bilu_factor_transpose, not bilu_factor
+ * (BILU_ERR_ARG).  p must not itself be a transposed pattern (BILU_ERR_ARG). */
+int bilu_pattern_transpose(const bilu_pattern* p, bilu_pattern** out);
+
+/* d_factors_t (device, bilu_factor_bytes(pt, b) bytes, laid out for pt) <-
+ * the factors of the source pattern of pt (d_factors, laid out for it) with
+ * every block transposed: [U'^T | D^{-T} | L^T].  pt must come from
+ * bilu_pattern_transpose and be uploaded (else BILU_ERR_ARG / BILU_ERR_STATE).
+ * Asynchronous; d_factors and d_factors_t must not overlap. */
+int bilu_factor_transpose(const bilu_pattern* pt, int32_t b, const double* d_factors, double* d_factors_t,
+                          void* stream);
+
+/* Transpose of a block CSR pattern (host, caller-allocated): row_ptr_t[n+1],
+ * col_idx_t[nnzb] (sorted rows) and perm[nnzb], the block of A that block t
+ * of A^T transposes.  BILU_ERR_PATTERN for an invalid row_ptr or column. */
+int bsr_transpose_pattern(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, int32_t* row_ptr_t,
+                          int32_t* col_idx_t, int32_t* perm);
+
+/* d_dst block t <- (d_src block d_perm[t])^T for t < nblocks (device arrays;
+ * b x b column-major blocks; A^T's values from A's with perm from
+ * bsr_transpose_pattern).  Indices are not checked on the device.
+ * Asynchronous; d_src and d_dst must not overlap. */
+int bsr_gather_transpose(int64_t nblocks, int32_t b, const int32_t* d_perm, const double* d_src, double* d_dst,
+                         void* stream);
+
+/* d_grad block t (row I, column J = col_idx[t]) <- -lambda_I x_J^T: the
+ * gradient of a loss with respect to A's blocks, given the adjoint solution
+ * lambda and the solution x (device arrays, n*b doubles each; d_grad has
+ * nnzb*b*b doubles).  Asynchronous. */
+int bsr_outer_grad(int32_t n, int32_t b, const int32_t* d_row_ptr, const int32_t* d_col_idx,
+                   const double* d_lambda, const double* d_x, double* d_grad, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -81,7 +81,8 @@ enum bilu_prof_kernel {
   BILU_PROF_SCALE_UPPER = 6,  /* factor: U' = D^{-1} U */
   BILU_PROF_KRYLOV = 7,       /* BiCGSTAB vector updates and reductions */
   BILU_PROF_FACTOR_INIT = 8,  /* factor: reset of the ready flags */
-  BILU_PROF_NKERNELS = 9
+  BILU_PROF_ADJOINT = 9,      /* adjoint: block gather-transposes and -lambda x^T */
+  BILU_PROF_NKERNELS = 10
 };
 
 /* Per-kernel timing: when on, every launch of the library is bracketed by

@@ -84,10 +84,15 @@ SIGNATURES = {
     "bilu_profile_read": (C.c_int, [C.c_int32, C.POINTER(C.c_int64), C.POINTER(C.c_double)]),
     "bilu_launch_count": (C.c_int64, []),
     "bilu_schedule_export": (C.c_int, [_vp, C.c_int32, _i32p, _i32p, _i32p, _i32p, _i32p, _i32p]),
+    "bilu_pattern_transpose": (C.c_int, [_vp, C.POINTER(_vp)]),
+    "bilu_factor_transpose": (C.c_int, [_vp, C.c_int32, _vp, _vp, _vp]),
+    "bsr_transpose_pattern": (C.c_int, [C.c_int32, _i32p, _i32p, _i32p, _i32p, _i32p]),
+    "bsr_gather_transpose": (C.c_int, [C.c_int64, C.c_int32, _vp, _vp, _vp, _vp]),
+    "bsr_outer_grad": (C.c_int, [C.c_int32, C.c_int32, _vp, _vp, _vp, _vp, _vp, _vp]),
 }
 
 PROF_KERNELS = ["spmv", "apply_prep", "lower_solve", "upper_solve", "backfill", "factor",
-                "scale_upper", "krylov_vector", "factor_init"]
+                "scale_upper", "krylov_vector", "factor_init", "adjoint"]
 
 _lib = None
 

@@ -123,6 +123,13 @@ class Pattern:
     def factor_bytes_f32(self, b: int) -> int:
         return int(L.load().bilu_factor_bytes_f32(self.handle, b))
 
+    def transpose(self, upload: bool = True) -> "Pattern":
+        """P'^T for the adjoint solve (bilu_pattern_transpose)."""
+        h = C.c_void_p()
+        _check(L.load().bilu_pattern_transpose(self.handle, C.byref(h)), "bilu_pattern_transpose")
+        pt = Pattern(h)
+        return pt.upload() if upload else pt
+
     def close(self):
         if self._h is not None:
             L.load().bilu_destroy_pattern(self._h)
@@ -355,3 +362,53 @@ def bilu_set_check_every(iters: int):
 
 def bilu_test_withhold_row(row: int):
     _check(L.load().bilu_test_withhold_row(row), "bilu_test_withhold_row")
+
+
+# ---- adjoint ----
+
+def bilu_factor_transpose(pattern_t: Pattern, b: int, factors: torch.Tensor,
+                          factors_t: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """Factors of P'^T ([U'^T | D^-T | L^T]) from those of P'."""
+    if factors_t is None:
+        factors_t = torch.empty_like(factors)
+    _check(L.load().bilu_factor_transpose(pattern_t.handle, b, _dev(factors, torch.float64, "factors"),
+                                          _dev(factors_t, torch.float64, "factors_t"), _stream_handle(stream)),
+           "bilu_factor_transpose")
+    return factors_t
+
+
+def bsr_transpose_pattern(n: int, row_ptr, col_idx):
+    """(row_ptr_t, col_idx_t, perm) of A^T on the host (bsr_transpose_pattern)."""
+    rp = _host_i32(row_ptr)
+    ci = _host_i32(col_idx)
+    nnz = int(rp[n]) if n > 0 else 0
+    rpt = np.zeros(n + 1, np.int32)
+    cit = np.zeros(max(nnz, 1), np.int32)
+    perm = np.zeros(max(nnz, 1), np.int32)
+    p = lambda a: a.ctypes.data_as(C.POINTER(C.c_int32))
+    _check(L.load().bsr_transpose_pattern(n, p(rp), p(ci), p(rpt), p(cit), p(perm)), "bsr_transpose_pattern")
+    return rpt, cit[:nnz], perm[:nnz]
+
+
+def bsr_gather_transpose(b: int, perm: torch.Tensor, src: torch.Tensor, dst: torch.Tensor | None = None,
+                         stream=None) -> torch.Tensor:
+    """dst block t = (src block perm[t])^T on the device."""
+    nblocks = perm.numel()
+    if dst is None:
+        dst = torch.empty(nblocks * b * b, dtype=torch.float64, device=src.device)
+    _check(L.load().bsr_gather_transpose(nblocks, b, _dev(perm, torch.int32, "perm"),
+                                         _dev(src, torch.float64, "src"), _dev(dst, torch.float64, "dst"),
+                                         _stream_handle(stream)), "bsr_gather_transpose")
+    return dst
+
+
+def bsr_outer_grad(n: int, b: int, row_ptr: torch.Tensor, col_idx: torch.Tensor, lam: torch.Tensor,
+                   x: torch.Tensor, grad: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """grad block (I, J) = -lambda_I x_J^T on A's block pattern."""
+    if grad is None:
+        grad = torch.empty(col_idx.numel() * b * b, dtype=torch.float64, device=x.device)
+    _check(L.load().bsr_outer_grad(n, b, _dev(row_ptr, torch.int32, "row_ptr"),
+                                   _dev(col_idx, torch.int32, "col_idx"), _dev(lam, torch.float64, "lambda"),
+                                   _dev(x, torch.float64, "x"), _dev(grad, torch.float64, "grad"),
+                                   _stream_handle(stream)), "bsr_outer_grad")
+    return grad

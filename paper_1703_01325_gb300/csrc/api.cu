@@ -99,7 +99,7 @@ extern "C" int bilu_pattern_upload(bilu_pattern* p, void* stream) {
   p->d_mem = mem;
   p->device = dev;
   if (ensure_schedule(p, &p->solve, trisolve_config().chunk, true) != 0 ||
-      ensure_schedule(p, &p->fact, trisolve_config().factor_chunk, false) != 0)
+      (!p->is_transpose && ensure_schedule(p, &p->fact, trisolve_config().factor_chunk, false) != 0))
     return BILU_ERR_OOM;
   return BILU_OK;
 }
@@ -132,7 +132,7 @@ int factor_impl(const bilu_pattern* p, int32_t b, const double* d_a_vals, TV* d_
     info->bad_row = -1;
     info->ms = 0.0;
   }
-  if (!p || !valid_b(b)) return BILU_ERR_ARG;
+  if (!p || !valid_b(b) || p->is_transpose) return BILU_ERR_ARG;
   int st = ready(p);
   if (st) return st;
   if (p->n > 0 && (!d_a_vals || !d_factors || !d_work)) return BILU_ERR_ARG;
@@ -380,4 +380,32 @@ extern "C" int bilu_schedule_export(const bilu_pattern* p, int32_t rows, int32_t
     put(tick_upper, tmp.tick_u);
   }
   return BILU_OK;
+}
+
+// ---- adjoint ----
+
+extern "C" int bilu_factor_transpose(const bilu_pattern* pt, int32_t b, const double* d_factors,
+                                     double* d_factors_t, void* stream) {
+  if (!pt || !valid_b(b) || !pt->is_transpose) return BILU_ERR_ARG;
+  int st = ready(pt);
+  if (st) return st;
+  if (pt->n == 0) return BILU_OK;
+  if (!d_factors || !d_factors_t || (const void*)d_factors == (const void*)d_factors_t) return BILU_ERR_ARG;
+  return cuda_status(launch_gather_transpose(pt->nslots(), b, pt->d_slot_src, d_factors, d_factors_t, stream));
+}
+
+extern "C" int bsr_gather_transpose(int64_t nblocks, int32_t b, const int32_t* d_perm, const double* d_src,
+                                    double* d_dst, void* stream) {
+  if (nblocks < 0 || !valid_b(b)) return BILU_ERR_ARG;
+  if (nblocks == 0) return BILU_OK;
+  if (!d_perm || !d_src || !d_dst || (const void*)d_src == (const void*)d_dst) return BILU_ERR_ARG;
+  return cuda_status(launch_gather_transpose(nblocks, b, d_perm, d_src, d_dst, stream));
+}
+
+extern "C" int bsr_outer_grad(int32_t n, int32_t b, const int32_t* d_row_ptr, const int32_t* d_col_idx,
+                              const double* d_lambda, const double* d_x, double* d_grad, void* stream) {
+  if (n < 0 || !valid_b(b)) return BILU_ERR_ARG;
+  if (n == 0) return BILU_OK;
+  if (!d_row_ptr || !d_col_idx || !d_lambda || !d_x || !d_grad) return BILU_ERR_ARG;
+  return cuda_status(launch_outer_grad(n, b, d_row_ptr, d_col_idx, d_lambda, d_x, d_grad, stream));
 }

@@ -43,8 +43,11 @@ struct bilu_pattern {
   // Strictly lower / strictly upper parts of P' as separate CSR structures.
   std::vector<int32_t> lrp, lci, urp, uci;
   // Backfill gather map: for every factor slot in [L | D | U] the A block that
-  // lands there, or -1 for a fill block (Algorithm 5 steps 3-4).
+  // lands there, or -1 for a fill block (Algorithm 5 steps 3-4).  For a
+  // transposed pattern (is_transpose): the slot of the source pattern's factor
+  // buffer whose transposed block lands there.
   std::vector<int32_t> slot_src;
+  bool is_transpose = false;
   // Schedules of the triangular solves and of the factorization (L only);
   // each has its own chunk size.
   bilu_chunk_schedule solve, fact;
@@ -129,6 +132,10 @@ void build_schedule(const bilu_pattern* p, int32_t chunk, bool upper, bilu_chunk
 void free_schedule(bilu_chunk_schedule* s);
 int launch_apply(const bilu_pattern* p, int32_t b, const double* f, const double* r, double* x,
                  void* work, int32_t* stop, void* stream);
+int launch_gather_transpose(long long nblocks, int32_t b, const int32_t* idx, const double* src, double* dst,
+                            void* stream);
+int launch_outer_grad(int32_t n, int32_t b, const int32_t* rp, const int32_t* ci, const double* lam,
+                      const double* x, double* grad, void* stream);
 int launch_apply_f32(const bilu_pattern* p, int32_t b, const float* f, const double* r, double* x,
                      void* work, int32_t* stop, void* stream);
 

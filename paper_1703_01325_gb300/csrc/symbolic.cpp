@@ -46,6 +46,54 @@ int check_pattern(int32_t n, const int32_t* rp, const int32_t* ci) {
   return BILU_OK;
 }
 
+// Eq. 4 levels and the L / U' split of a pattern whose rp, ci (and n) are set.
+void finish_pattern(bilu_pattern* p) {
+  const int32_t n = p->n;
+  // Eq. 4 on the lower part (rows ascending) and on the reversed graph of the
+  // upper part (rows descending); 0-based.
+  p->lvl_l.assign((size_t)n, 0);
+  p->lvl_u.assign((size_t)n, 0);
+  int32_t ml = -1, mu = -1;
+  for (int32_t i = 0; i < n; ++i) {
+    int32_t l = 0;
+    for (int32_t t = p->rp[i]; t < p->rp[i + 1] && p->ci[t] < i; ++t)
+      l = std::max(l, p->lvl_l[p->ci[t]] + 1);
+    p->lvl_l[i] = l;
+    ml = std::max(ml, l);
+  }
+  for (int32_t i = n - 1; i >= 0; --i) {
+    int32_t l = 0;
+    for (int32_t t = p->rp[i + 1] - 1; t >= p->rp[i] && p->ci[t] > i; --t)
+      l = std::max(l, p->lvl_u[p->ci[t]] + 1);
+    p->lvl_u[i] = l;
+    mu = std::max(mu, l);
+  }
+  p->nlev_l = ml + 1;
+  p->nlev_u = mu + 1;
+
+  // Split P' into strictly lower and strictly upper CSR structures.
+  p->lrp.assign((size_t)n + 1, 0);
+  p->urp.assign((size_t)n + 1, 0);
+  for (int32_t i = 0; i < n; ++i) {
+    int32_t nl = 0, nu = 0;
+    for (int32_t t = p->rp[i]; t < p->rp[i + 1]; ++t) {
+      if (p->ci[t] < i) ++nl;
+      else if (p->ci[t] > i) ++nu;
+    }
+    p->lrp[(size_t)i + 1] = p->lrp[i] + nl;
+    p->urp[(size_t)i + 1] = p->urp[i] + nu;
+  }
+  p->lci.resize((size_t)p->lrp[n]);
+  p->uci.resize((size_t)p->urp[n]);
+  for (int32_t i = 0; i < n; ++i) {
+    int32_t a = p->lrp[i], c = p->urp[i];
+    for (int32_t t = p->rp[i]; t < p->rp[i + 1]; ++t) {
+      if (p->ci[t] < i) p->lci[a++] = p->ci[t];
+      else if (p->ci[t] > i) p->uci[c++] = p->ci[t];
+    }
+  }
+}
+
 }  // namespace
 
 extern "C" int bilu_symbolic(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, int32_t k,
@@ -110,49 +158,7 @@ extern "C" int bilu_symbolic(int32_t n, const int32_t* row_ptr, const int32_t* c
       p->rp[(size_t)i + 1] = (int32_t)p->ci.size();
     }
 
-    // Eq. 4 on the lower part (rows ascending) and on the reversed graph of the
-    // upper part (rows descending); 0-based.
-    p->lvl_l.assign((size_t)n, 0);
-    p->lvl_u.assign((size_t)n, 0);
-    int32_t ml = -1, mu = -1;
-    for (int32_t i = 0; i < n; ++i) {
-      int32_t l = 0;
-      for (int32_t t = p->rp[i]; t < p->rp[i + 1] && p->ci[t] < i; ++t)
-        l = std::max(l, p->lvl_l[p->ci[t]] + 1);
-      p->lvl_l[i] = l;
-      ml = std::max(ml, l);
-    }
-    for (int32_t i = n - 1; i >= 0; --i) {
-      int32_t l = 0;
-      for (int32_t t = p->rp[i + 1] - 1; t >= p->rp[i] && p->ci[t] > i; --t)
-        l = std::max(l, p->lvl_u[p->ci[t]] + 1);
-      p->lvl_u[i] = l;
-      mu = std::max(mu, l);
-    }
-    p->nlev_l = ml + 1;
-    p->nlev_u = mu + 1;
-
-    // Split P' into strictly lower and strictly upper CSR structures.
-    p->lrp.assign((size_t)n + 1, 0);
-    p->urp.assign((size_t)n + 1, 0);
-    for (int32_t i = 0; i < n; ++i) {
-      int32_t nl = 0, nu = 0;
-      for (int32_t t = p->rp[i]; t < p->rp[i + 1]; ++t) {
-        if (p->ci[t] < i) ++nl;
-        else if (p->ci[t] > i) ++nu;
-      }
-      p->lrp[(size_t)i + 1] = p->lrp[i] + nl;
-      p->urp[(size_t)i + 1] = p->urp[i] + nu;
-    }
-    p->lci.resize((size_t)p->lrp[n]);
-    p->uci.resize((size_t)p->urp[n]);
-    for (int32_t i = 0; i < n; ++i) {
-      int32_t a = p->lrp[i], c = p->urp[i];
-      for (int32_t t = p->rp[i]; t < p->rp[i + 1]; ++t) {
-        if (p->ci[t] < i) p->lci[a++] = p->ci[t];
-        else if (p->ci[t] > i) p->uci[c++] = p->ci[t];
-      }
-    }
+    finish_pattern(p);
 
     // Backfill gather map (Algorithm 5 steps 3-4): slot -> A block or -1.
     const int64_t nl = p->nnz_l(), nslots = p->nslots();
@@ -183,6 +189,90 @@ extern "C" int bilu_symbolic(int32_t n, const int32_t* row_ptr, const int32_t* c
     return BILU_ERR_OOM;
   }
   *out = p;
+  return BILU_OK;
+}
+
+// P'^T for the adjoint solve with A^T (its lower part is the transpose of U',
+// its upper part the transpose of L), with Eq. 4 levels and the map from each
+// of its factor slots to the slot of P' that holds the block to transpose.
+extern "C" int bilu_pattern_transpose(const bilu_pattern* p, bilu_pattern** out) {
+  if (!p || !out || p->is_transpose) return BILU_ERR_ARG;
+  *out = nullptr;
+  bilu_pattern* q = new (std::nothrow) bilu_pattern();
+  if (!q) return BILU_ERR_OOM;
+  try {
+    const int32_t n = p->n;
+    const size_t nnz = p->ci.size();
+    q->n = n;
+    q->k = p->k;
+    q->nnz_a = p->nnz_a;
+    q->is_transpose = true;
+    // CSR transpose of P' (and of the entry levels); src[t'] = entry of P'
+    q->rp.assign((size_t)n + 1, 0);
+    for (size_t t = 0; t < nnz; ++t) ++q->rp[(size_t)p->ci[t] + 1];
+    for (int32_t i = 0; i < n; ++i) q->rp[(size_t)i + 1] += q->rp[i];
+    q->ci.resize(nnz);
+    q->lev.resize(nnz);
+    std::vector<int32_t> src(nnz), at(q->rp.begin(), q->rp.end() - 1);
+    for (int32_t i = 0; i < n; ++i)
+      for (int32_t t = p->rp[i]; t < p->rp[i + 1]; ++t) {
+        const int32_t d = at[p->ci[t]]++;
+        q->ci[d] = i;
+        q->lev[d] = p->lev[t];
+        src[d] = t;
+      }
+    finish_pattern(q);
+    // factor slot of every P' entry: [L | D | U] positions
+    auto slots = [](const bilu_pattern* m, std::vector<int32_t>& slot) {
+      slot.resize(m->ci.size());
+      const int64_t nl = m->nnz_l();
+      for (int32_t i = 0; i < m->n; ++i) {
+        int32_t a = m->lrp[i], c = m->urp[i];
+        for (int32_t t = m->rp[i]; t < m->rp[i + 1]; ++t) {
+          const int32_t j = m->ci[t];
+          slot[t] = j < i ? a++ : (j == i ? (int32_t)(nl + i) : (int32_t)(nl + m->n + c++));
+        }
+      }
+    };
+    std::vector<int32_t> sp, sq;
+    slots(p, sp);
+    slots(q, sq);
+    q->slot_src.assign((size_t)q->nslots(), -1);
+    for (size_t d = 0; d < nnz; ++d) q->slot_src[(size_t)sq[d]] = sp[(size_t)src[d]];
+  } catch (const std::bad_alloc&) {
+    delete q;
+    return BILU_ERR_OOM;
+  }
+  *out = q;
+  return BILU_OK;
+}
+
+// Transpose of a block CSR pattern (host): row_ptr_t / col_idx_t of A^T and,
+// for every block of A^T, the block of A it transposes.
+extern "C" int bsr_transpose_pattern(int32_t n, const int32_t* row_ptr, const int32_t* col_idx,
+                                     int32_t* row_ptr_t, int32_t* col_idx_t, int32_t* perm) {
+  if (n < 0 || !row_ptr || !row_ptr_t || (n > 0 && row_ptr[n] > 0 && (!col_idx || !col_idx_t || !perm)))
+    return BILU_ERR_ARG;
+  if (row_ptr[0] != 0) return BILU_ERR_PATTERN;
+  for (int32_t i = 0; i < n; ++i)
+    if (row_ptr[i + 1] < row_ptr[i]) return BILU_ERR_PATTERN;
+  const int32_t nnz = n > 0 ? row_ptr[n] : 0;
+  for (int32_t t = 0; t < nnz; ++t)
+    if (col_idx[t] < 0 || col_idx[t] >= n) return BILU_ERR_PATTERN;
+  std::fill(row_ptr_t, row_ptr_t + (size_t)n + 1, 0);
+  for (int32_t t = 0; t < nnz; ++t) ++row_ptr_t[col_idx[t] + 1];
+  for (int32_t i = 0; i < n; ++i) row_ptr_t[i + 1] += row_ptr_t[i];
+  try {
+    std::vector<int32_t> at(row_ptr_t, row_ptr_t + n);
+    for (int32_t i = 0; i < n; ++i)
+      for (int32_t t = row_ptr[i]; t < row_ptr[i + 1]; ++t) {
+        const int32_t d = at[col_idx[t]]++;
+        col_idx_t[d] = i;
+        perm[d] = t;
+      }
+  } catch (const std::bad_alloc&) {
+    return BILU_ERR_OOM;
+  }
   return BILU_OK;
 }
 
