@@ -50,9 +50,11 @@ def lib():
         L.or_spmv.argtypes = [C.c_int32, C.c_int32, i32p, i32p, f64p, f64p, f64p]
         L.or_bicgstab.argtypes = [C.c_int32, C.c_int32, i32p, i32p, f64p, i32p, i32p, f64p, f64p,
                                   f64p, f64p, C.c_double, C.c_int32, i32p, f64p]
+        L.or_gmres.argtypes = [C.c_int32, C.c_int32, i32p, i32p, f64p, i32p, i32p, f64p, f64p,
+                               f64p, f64p, C.c_double, C.c_int32, C.c_int32, i32p, f64p]
         L.or_free.argtypes = [C.c_void_p]
         for f in ("or_check_pattern", "or_symbolic", "or_levels", "or_backfill", "or_factor",
-                  "or_apply", "or_spmv", "or_bicgstab"):
+                  "or_apply", "or_spmv", "or_bicgstab", "or_gmres"):
             getattr(L, f).restype = C.c_int
     return _lib
 
@@ -178,4 +180,26 @@ def bicgstab(n, b, rp, ci, vals, prp, pci, F, dinv, rhs, x0=None, tol=1e-8, maxi
     st = lib().or_bicgstab(n, b, a, c, v, pp, pc, pf, pd, prh,
                            x.ctypes.data_as(C.POINTER(C.c_double)), tol, maxit,
                            C.byref(it), C.byref(rr))
+    return x[: n * b], it.value, rr.value, st
+
+
+def gmres(n, b, rp, ci, vals, prp, pci, F, dinv, rhs, x0=None, tol=1e-8, maxit=1000, restart=20):
+    """Restarted GMRES(restart), right-preconditioned.  Returns (x, iters,
+    true_relres, status)."""
+    rp, a = _i32(rp)
+    ci, c = _i32(ci)
+    vals, v = _f64(vals)
+    prp, pp = _i32(prp)
+    pci, pc = _i32(pci)
+    F, pf = _f64(F)
+    dinv, pd = _f64(dinv)
+    rhs, prh = _f64(rhs)
+    x = np.zeros(max(n * b, 1), np.float64)
+    if x0 is not None:
+        x[: n * b] = x0
+    it = C.c_int32(0)
+    rr = C.c_double(0.0)
+    st = lib().or_gmres(n, b, a, c, v, pp, pc, pf, pd, prh,
+                        x.ctypes.data_as(C.POINTER(C.c_double)), tol, maxit, restart,
+                        C.byref(it), C.byref(rr))
     return x[: n * b], it.value, rr.value, st

@@ -443,3 +443,103 @@ int or_bicgstab(int32_t n, int32_t b, const int32_t* rp, const int32_t* ci,
   free(buf);
   return status;
 }
+
+/* ------------------------------------------------------------------------- */
+/* Restarted GMRES(m), right preconditioning (see bilu_oracle.h).             */
+/* ------------------------------------------------------------------------- */
+int or_gmres(int32_t n, int32_t b, const int32_t* rp, const int32_t* ci,
+             const double* vals, const int32_t* prp, const int32_t* pci,
+             const double* fvals, const double* dinv, const double* rhs,
+             double* x, double tol, int32_t maxit, int32_t m, int32_t* iters,
+             double* relres) {
+  if (n < 0 || b < 1 || b > 8 || maxit < 0 || m < 1 || m > 64 || !(tol >= 0.0)) return OR_ERR_ARG;
+  size_t len = (size_t)n * b;
+  *iters = 0;
+  *relres = 0.0;
+  double bnorm = sqrt(vdot(len, rhs, rhs));
+  if (bnorm == 0.0) {
+    for (size_t q = 0; q < len; ++q) x[q] = 0.0;
+    return OR_OK;
+  }
+  /* V: m+1 basis vectors; w, z, u: work vectors; H column-major (m+1) x m */
+  double* buf = (double*)malloc(sizeof(double) * ((size_t)(m + 4) * len + 8));
+  double* H = (double*)malloc(sizeof(double) * (size_t)(m + 1) * m);
+  double* cs = (double*)malloc(sizeof(double) * (size_t)m);
+  double* sn = (double*)malloc(sizeof(double) * (size_t)m);
+  double* g = (double*)malloc(sizeof(double) * (size_t)(m + 1));
+  double* y = (double*)malloc(sizeof(double) * (size_t)m);
+  if (!buf || !H || !cs || !sn || !g || !y) {
+    free(buf); free(H); free(cs); free(sn); free(g); free(y);
+    return OR_ERR_OOM;
+  }
+  double* V = buf;
+  double* w = V + (size_t)(m + 1) * len;
+  double* z = w + len;
+  double* u = z + len;
+  int status = OR_ERR_NOT_CONVERGED;
+  int32_t it = 0;
+  for (;;) {
+    /* r0 = b - A x */
+    or_spmv(n, b, rp, ci, vals, x, w);
+    for (size_t q = 0; q < len; ++q) w[q] = rhs[q] - w[q];
+    double beta = sqrt(vdot(len, w, w));
+    *relres = beta / bnorm;
+    if (*relres <= tol) { status = OR_OK; break; }
+    if (it >= maxit) { status = OR_ERR_NOT_CONVERGED; break; }
+    for (size_t q = 0; q < len; ++q) V[q] = w[q] / beta;
+    for (int32_t q = 0; q <= m; ++q) g[q] = 0.0;
+    g[0] = beta;
+    int32_t k = 0; /* columns of this cycle */
+    while (k < m && it < maxit) {
+      int32_t j = k;
+      double* vj = V + (size_t)j * len;
+      or_apply(n, b, prp, pci, fvals, dinv, vj, z);
+      or_spmv(n, b, rp, ci, vals, z, w);
+      double* hj = H + (size_t)j * (m + 1);
+      for (int32_t i = 0; i <= j; ++i) { /* modified Gram-Schmidt */
+        const double* vi = V + (size_t)i * len;
+        hj[i] = vdot(len, w, vi);
+        for (size_t q = 0; q < len; ++q) w[q] -= hj[i] * vi[q];
+      }
+      hj[j + 1] = sqrt(vdot(len, w, w));
+      /* previous rotations on column j, then the new one */
+      for (int32_t i = 0; i < j; ++i) {
+        double a = hj[i], c = hj[i + 1];
+        hj[i] = cs[i] * a + sn[i] * c;
+        hj[i + 1] = -sn[i] * a + cs[i] * c;
+      }
+      double a = hj[j], c = hj[j + 1];
+      double rho = sqrt(a * a + c * c);
+      ++it;
+      k = j + 1;
+      if (rho == 0.0) { k = j; break; } /* w and v_j both vanish: no progress */
+      cs[j] = a / rho;
+      sn[j] = c / rho;
+      hj[j] = rho;
+      hj[j + 1] = 0.0;
+      g[j + 1] = -sn[j] * g[j];
+      g[j] = cs[j] * g[j];
+      if (fabs(g[j + 1]) <= tol * bnorm) break;
+      if (c == 0.0) break; /* h_{j+1,j} = 0: the Krylov space is invariant */
+      double* vn = V + (size_t)(j + 1) * len;
+      for (size_t q = 0; q < len; ++q) vn[q] = w[q] / c;
+    }
+    if (k == 0) { status = OR_ERR_BREAKDOWN; break; }
+    /* y = R^{-1} g by back substitution; u = V y; x += M^{-1} u */
+    for (int32_t i = k - 1; i >= 0; --i) {
+      double s = g[i];
+      for (int32_t l = i + 1; l < k; ++l) s -= H[(size_t)l * (m + 1) + i] * y[l];
+      y[i] = s / H[(size_t)i * (m + 1) + i];
+    }
+    for (size_t q = 0; q < len; ++q) u[q] = 0.0;
+    for (int32_t i = 0; i < k; ++i) {
+      const double* vi = V + (size_t)i * len;
+      for (size_t q = 0; q < len; ++q) u[q] += y[i] * vi[q];
+    }
+    or_apply(n, b, prp, pci, fvals, dinv, u, z);
+    for (size_t q = 0; q < len; ++q) x[q] += z[q];
+  }
+  *iters = it;
+  free(buf); free(H); free(cs); free(sn); free(g); free(y);
+  return status;
+}

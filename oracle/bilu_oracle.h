@@ -94,6 +94,25 @@ int or_bicgstab(int32_t n, int32_t b, const int32_t* rp, const int32_t* ci,
                 double* x, double tol, int32_t maxit, int32_t* iters,
                 double* relres);
 
+/* Restarted GMRES(m) preconditioned on the right with M = L D U' -- the
+ * solver of the paper's experiments (Section 4: GMRES restarted every 20
+ * iterations).  Each cycle: r0 = b - A x, beta = ||r0||, v_1 = r0 / beta;
+ * for j = 1..m the Arnoldi step w = A M^{-1} v_j orthogonalised by modified
+ * Gram-Schmidt (h_ij = (w, v_i), w -= h_ij v_i for i = 1..j, in order),
+ * h_{j+1,j} = ||w||, v_{j+1} = w / h_{j+1,j}; Givens rotations reduce H to
+ * upper triangular form and |g_{j+1}| is the residual norm of the least
+ * squares problem min ||beta e_1 - H y||.  The cycle ends when |g_{j+1}| <=
+ * tol ||b||, when h_{j+1,j} = 0, after m steps, or when maxit steps have been
+ * taken in all; then y solves the triangular system and x += M^{-1} (V y).
+ * The solve stops once the recomputed true residual ||b - A x|| / ||b|| <=
+ * tol, otherwise the next cycle starts from it.  *iters counts Arnoldi steps;
+ * *relres is the true relative residual of the returned x.  1 <= m <= 64. */
+int or_gmres(int32_t n, int32_t b, const int32_t* rp, const int32_t* ci,
+             const double* vals, const int32_t* prp, const int32_t* pci,
+             const double* fvals, const double* dinv, const double* rhs,
+             double* x, double tol, int32_t maxit, int32_t m, int32_t* iters,
+             double* relres);
+
 void or_free(void* p);
 
 #ifdef __cplusplus

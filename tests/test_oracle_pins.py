@@ -433,3 +433,85 @@ def test_bicgstab_first_step_properties():
     t = A @ s_hat
     omega = np.linalg.lstsq(t[:, None], s, rcond=None)[0][0]
     assert np.allclose(x1, alpha * p_hat + omega * s_hat, rtol=1e-10, atol=1e-12 * np.abs(x1).max())
+
+
+# ----------------------------------------------------------------------------
+# Restarted GMRES(m) (the solver of the paper's experiments, Section 4)
+# ----------------------------------------------------------------------------
+
+def _gmres_system(seed=31, b=2, k=0):
+    S = reservoir_system(4, 4, 3, b, sigma=1.0, accum=0.01, seed=seed)
+    prp, pci, _ = oracle.symbolic(S.n, S.row_ptr, S.col_idx, k)
+    F, dinv = oracle.factor(S.n, b, prp, pci, oracle.backfill(S.n, b, S.row_ptr, S.col_idx, S.vals, prp, pci))
+    L, D, U = split_factors(S.n, b, prp, pci, F)
+    A = to_dense(S.n, b, S.row_ptr, S.col_idx, S.vals)
+    return S, prp, pci, F, dinv, A, L @ D @ U
+
+
+def _min_residual_point(A, Minv, x0, r0, j):
+    """argmin ||b - A x|| over x0 + M^{-1} K_j(A M^{-1}, r0), by brute force:
+    an orthonormal basis of the Krylov space (numpy QR) and least squares."""
+    AM = A @ Minv
+    K = np.empty((len(r0), j))
+    v = r0.copy()
+    for q in range(j):
+        K[:, q] = v / np.linalg.norm(v)
+        v = AM @ K[:, q]
+    Q, _ = np.linalg.qr(K)
+    c = np.linalg.lstsq(AM @ Q, r0, rcond=None)[0]
+    return x0 + Minv @ (Q @ c)
+
+
+@pytest.mark.parametrize("j", [1, 2, 4, 7])
+def test_gmres_minimises_the_residual_over_the_krylov_space(j):
+    """After j Arnoldi steps from x0 = 0 (no restart), x_j is the minimal
+    residual point of x0 + M^{-1} K_j(A M^{-1}, b)."""
+    S, prp, pci, F, dinv, A, M = _gmres_system()
+    x, it, rr, st = oracle.gmres(S.n, S.b, S.row_ptr, S.col_idx, S.vals, prp, pci, F, dinv, S.rhs,
+                                 tol=1e-30, maxit=j, restart=20)
+    assert it == j and st == oracle.ERR_NOT_CONVERGED
+    xm = _min_residual_point(A, np.linalg.inv(M), np.zeros_like(S.rhs), S.rhs, j)
+    assert np.linalg.norm(x - xm) <= 1e-8 * np.linalg.norm(xm)
+    assert np.linalg.norm(S.rhs - A @ x) / np.linalg.norm(S.rhs) == pytest.approx(rr, rel=1e-9)
+
+
+def test_gmres_restart_starts_from_the_true_residual():
+    """GMRES(3) with 5 steps: one full cycle (minimal residual over K_3), then a
+    cycle of 2 steps from r_3 = b - A x_3."""
+    S, prp, pci, F, dinv, A, M = _gmres_system(seed=32)
+    Minv = np.linalg.inv(M)
+    x, it, rr, st = oracle.gmres(S.n, S.b, S.row_ptr, S.col_idx, S.vals, prp, pci, F, dinv, S.rhs,
+                                 tol=1e-30, maxit=5, restart=3)
+    assert it == 5
+    x3 = _min_residual_point(A, Minv, np.zeros_like(S.rhs), S.rhs, 3)
+    x5 = _min_residual_point(A, Minv, x3, S.rhs - A @ x3, 2)
+    assert np.linalg.norm(x - x5) <= 1e-8 * np.linalg.norm(x5)
+
+
+@pytest.mark.parametrize("k", [0, 1])
+def test_gmres_solves_small_reservoir(k):
+    S = reservoir_system(6, 5, 4, 3, sigma=1.0, accum=0.01)
+    prp, pci, _ = oracle.symbolic(S.n, S.row_ptr, S.col_idx, k)
+    F, dinv = oracle.factor(S.n, 3, prp, pci, oracle.backfill(S.n, 3, S.row_ptr, S.col_idx, S.vals, prp, pci))
+    x, it, rr, st = oracle.gmres(S.n, 3, S.row_ptr, S.col_idx, S.vals, prp, pci, F, dinv, S.rhs,
+                                 tol=1e-10, maxit=2000, restart=20)
+    assert st == oracle.OK and rr <= 1e-10 and it > 0
+    Ad = to_dense(S.n, 3, S.row_ptr, S.col_idx, S.vals)
+    xd = np.linalg.solve(Ad, S.rhs)
+    assert np.linalg.norm(x - xd) <= 1e-10 * np.linalg.cond(Ad) * np.linalg.norm(xd)
+    assert np.linalg.norm(Ad @ x - S.rhs) / np.linalg.norm(S.rhs) == pytest.approx(rr, rel=1e-6)
+
+
+def test_gmres_exact_preconditioner_one_step_and_edges():
+    n, b = 10, 2
+    rp, ci = random_pattern(n, density=0.3, seed=11)
+    vals = diag_dominant_block_values(n, b, rp, ci, seed=12)
+    prp, pci, _ = oracle.symbolic(n, rp, ci, n)
+    F, dinv = oracle.factor(n, b, prp, pci, oracle.backfill(n, b, rp, ci, vals, prp, pci))
+    rhs = np.linspace(1, 2, n * b)
+    x, it, rr, st = oracle.gmres(n, b, rp, ci, vals, prp, pci, F, dinv, rhs, tol=1e-12, maxit=10)
+    assert st == oracle.OK and it == 1 and rr <= 1e-12
+    x, it, rr, st = oracle.gmres(n, b, rp, ci, vals, prp, pci, F, dinv, np.zeros(n * b), tol=1e-8, maxit=10)
+    assert st == oracle.OK and it == 0 and not x.any()
+    x, it, rr, st = oracle.gmres(n, b, rp, ci, vals, prp, pci, F, dinv, rhs, tol=1e-8, maxit=0)
+    assert st == oracle.ERR_NOT_CONVERGED and it == 0 and not x.any()
