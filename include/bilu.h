@@ -343,6 +343,30 @@ int bicgstab_solve_mixed(const bilu_pattern* p, const bilu_bsr* A, const float* 
                          int32_t maxit, double inner_tol, int32_t inner_maxit, void* d_work,
                          size_t work_bytes, void* stream, bilu_solve_info* info);
 
+/* Scratch bytes gmres_solve needs for restart length `restart` (0 for invalid
+ * arguments). */
+size_t gmres_workspace_bytes(const bilu_pattern* p, int32_t b, int32_t restart);
+
+/*
+ * gmres_solve -- restarted GMRES(restart) preconditioned on the right with
+ * M = L D U', the solver of the paper's experiments (Section 4 restarts it
+ * every 20 iterations).  Each cycle starts from r0 = rhs - A x, builds an
+ * Arnoldi basis of A M^{-1} by modified Gram-Schmidt, reduces the Hessenberg
+ * matrix with Givens rotations and ends when the least-squares residual is
+ * <= tol ||rhs||, when the Krylov space is invariant, after `restart` steps or
+ * when maxit steps have been taken in all; then x += M^{-1} V y.  The solve
+ * returns BILU_OK once the recomputed true residual ||rhs - A x|| / ||rhs|| <=
+ * tol, else starts the next cycle (BILU_ERR_NOT_CONVERGED after maxit steps,
+ * BILU_ERR_BREAKDOWN when a cycle makes no step).
+ *   restart in [1, 64]; tol in (0, 1); maxit >= 0 counts Arnoldi steps.
+ *   Other arguments as for bicgstab_solve; d_work holds
+ *   gmres_workspace_bytes(p, A->b, restart) bytes.  info->iters counts
+ *   Arnoldi steps.  Synchronises the stream every few steps.
+ */
+int gmres_solve(const bilu_pattern* p, const bilu_bsr* A, const double* d_factors, const double* d_rhs,
+                double* d_x, double tol, int32_t maxit, int32_t restart, void* d_work, size_t work_bytes,
+                void* stream, bilu_solve_info* info);
+
 /* ---- adjoint: A^T lambda = g with the transposed factors ----
  *
  * A loss L(x) through x = A^{-1} b has dL/db = lambda and dL/dA_IJ =

@@ -252,6 +252,30 @@ def bicgstab_solve(pattern: Pattern, A, factors: torch.Tensor, rhs: torch.Tensor
     return x, info
 
 
+def gmres_solve(pattern: Pattern, A, factors: torch.Tensor, rhs: torch.Tensor, x: torch.Tensor | None = None,
+                tol: float = 1e-8, maxit: int = 1000, restart: int = 20, work: torch.Tensor | None = None,
+                stream=None):
+    """Restarted GMRES(restart), right-preconditioned, on the device.  Same
+    conventions as bicgstab_solve; info.iters counts Arnoldi steps."""
+    n, b, rp, ci, vals = A
+    if x is None:
+        x = torch.zeros_like(rhs)
+    if work is None:
+        nb = int(L.load().gmres_workspace_bytes(pattern.handle, b, restart))
+        if nb == 0:
+            _check(L.BILU_ERR_ARG, "gmres_workspace_bytes")
+        work = workspace(nb, rhs.device)
+    bsr = L.BSR(n, b, _dev(rp, torch.int32, "row_ptr"), _dev(ci, torch.int32, "col_idx"),
+                _dev(vals, torch.float64, "vals"))
+    info = L.SolveInfo()
+    st = L.load().gmres_solve(pattern.handle, C.byref(bsr), _dev(factors, torch.float64, "factors"),
+                              _dev(rhs, torch.float64, "rhs"), _dev(x, torch.float64, "x"), tol, maxit, restart,
+                              _dev(work, torch.uint8, "work"), work.numel(), _stream_handle(stream), C.byref(info))
+    if st in (L.BILU_ERR_ARG, L.BILU_ERR_STATE, L.BILU_ERR_CUDA, L.BILU_ERR_OOM):
+        _check(st, "gmres_solve")
+    return x, info
+
+
 # ---- mixed precision ----
 
 def bilu_convert_f32(src: torch.Tensor, dst: torch.Tensor | None = None, stream=None) -> torch.Tensor:

@@ -17,7 +17,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libbilu.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["api.cu", "spmv.cu", "trisolve.cu", "factor.cu", "krylov.cu", "adjoint.cu", "profile.cu", "noalloc.cu",
+SOURCES = ["api.cu", "spmv.cu", "trisolve.cu", "factor.cu", "krylov.cu", "gmres.cu", "adjoint.cu", "profile.cu", "noalloc.cu",
            "symbolic.cpp"]
 
 

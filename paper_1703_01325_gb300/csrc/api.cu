@@ -254,6 +254,37 @@ extern "C" int bicgstab_solve(const bilu_pattern* p, const bilu_bsr* A, const do
   return run_bicgstab(p, A, d_factors, d_rhs, d_x, tol, maxit, d_work, stream, info, g_check_every);
 }
 
+extern "C" size_t gmres_workspace_bytes(const bilu_pattern* p, int32_t b, int32_t restart) {
+  if (!p || !valid_b(b) || restart < 1 || restart > gmres_max_restart()) return 0;
+  return gmres_workspace_bytes_impl(p->n, b, restart);
+}
+
+extern "C" int gmres_solve(const bilu_pattern* p, const bilu_bsr* A, const double* d_factors, const double* d_rhs,
+                           double* d_x, double tol, int32_t maxit, int32_t restart, void* d_work,
+                           size_t work_bytes, void* stream, bilu_solve_info* info) {
+  if (info) {
+    info->status = BILU_ERR_ARG;
+    info->iters = 0;
+    info->true_relres = 0.0;
+    info->ms = 0.0;
+  }
+  if (!p || !A || !valid_b(A->b) || A->n != p->n || !(tol > 0.0) || maxit < 0 || restart < 1 ||
+      restart > gmres_max_restart())
+    return BILU_ERR_ARG;
+  int st = ready(p);
+  if (st) return st;
+  if (p->n == 0) {
+    if (info) info->status = BILU_OK;
+    return BILU_OK;
+  }
+  if (!A->row_ptr || !A->col_idx || !A->vals || !d_factors || !d_rhs || !d_x || !d_work ||
+      (const void*)d_rhs == (const void*)d_x)
+    return BILU_ERR_ARG;
+  if (work_bytes < gmres_workspace_bytes_impl(p->n, A->b, restart)) return BILU_ERR_STATE;
+  if (solve_schedule(p) != 0) return BILU_ERR_OOM;
+  return run_gmres(p, A, d_factors, d_rhs, d_x, tol, maxit, restart, d_work, stream, info, g_check_every);
+}
+
 // ---- mixed precision ----
 
 extern "C" size_t bilu_factor_bytes_f32(const bilu_pattern* p, int32_t b) {

@@ -154,6 +154,10 @@ int bicgstab_core(const KOps& ops, long long m, const double* rhs, double* x, do
 int run_bicgstab_mixed(const bilu_pattern* p, const bilu_bsr* A, const float* vals32, const float* f32,
                        const double* rhs, double* x, double tol, int32_t maxit, double inner_tol,
                        int32_t inner_maxit, void* work, void* stream, bilu_solve_info* info, int batch);
+size_t gmres_workspace_bytes_impl(int32_t n, int32_t b, int32_t m);
+int gmres_max_restart();
+int run_gmres(const bilu_pattern* p, const bilu_bsr* A, const double* f, const double* rhs, double* x, double tol,
+              int32_t maxit, int32_t m, void* work, void* stream, bilu_solve_info* info, int batch);
 int run_bicgstab(const bilu_pattern* p, const bilu_bsr* A, const double* f, const double* rhs,
                  double* x, double tol, int32_t maxit, void* work, void* stream,
                  bilu_solve_info* info, int batch);

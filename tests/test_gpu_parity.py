@@ -310,3 +310,22 @@ def test_full_size_solve_fixed_iterations(B, full_size):
     assert sinfo.status in (4, 5) and sinfo.true_relres > 1e-8
     res = np.linalg.norm(S.rhs - o.spmv(x.cpu().numpy())) / np.linalg.norm(S.rhs)
     assert res == pytest.approx(sinfo.true_relres, rel=1e-6)
+
+
+def test_full_size_gmres_fixed_steps(B, full_size):
+    """GMRES(20) at full size, 12 Arnoldi steps (one cycle, no restart) and
+    25 steps (a restart after 20): the GPU iterate matches the oracle's to
+    1e-8 and the reported true residual is the oracle SpMV's."""
+    S, o, P, F, (rp, ci, vals, rhs), info = full_size
+    A = (S.n, 3, rp, ci, vals)
+    for steps in (12, 25):
+        x, sinfo = B.gmres_solve(P, A, F, rhs, tol=1e-30, maxit=steps, restart=20)
+        assert sinfo.status == 5 and sinfo.iters == steps
+        xo, ito, rro, sto = oracle.gmres(S.n, 3, S.row_ptr, S.col_idx, S.vals, o.prp, o.pci, o.F, o.Dinv,
+                                         S.rhs, tol=1e-30, maxit=steps, restart=20)
+        assert sto == oracle.ERR_NOT_CONVERGED and ito == steps
+        xg = x.cpu().numpy()
+        assert np.linalg.norm(xg - xo) <= TOL_X * np.linalg.norm(xo)
+        res = np.linalg.norm(S.rhs - o.spmv(xg)) / np.linalg.norm(S.rhs)
+        assert res == pytest.approx(sinfo.true_relres, rel=1e-6)
+        assert rro == pytest.approx(sinfo.true_relres, rel=1e-6)
