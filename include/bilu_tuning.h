@@ -37,10 +37,11 @@ int bilu_set_trisolve_warps(int32_t warps);
 /* Host copy of the schedule the sync-free solves use for a target of `rows`
  * rows per chunk (the same one bilu_apply builds; the factorization builds
  * one the same way for its own target).  Rows are cut into *nchunks chunks
- * of consecutive rows, chunk c = rows [bounds[c], bounds[c+1]); cuts fall
- * where a row neither depends on its predecessor (L) nor is depended on by
- * it (U'), the one nearest the target within [rows/2, 2*rows] (at most 1024
- * rows), else at the target.
+ * of consecutive rows, chunk c = rows [bounds[c], bounds[c+1]).  A cut falls
+ * before the row farthest from its nearest dependency (the largest gap
+ * r - max{j < r in L(r)}, and likewise for U') among the rows with a gap > 1
+ * in [rows/2, 3*rows/2] (at most 1024) rows from the chunk's start, the one
+ * nearest the target among equal gaps; else at the target.
  *   bounds (n + 1 entries capacity): the cut rows, bounds[0] = 0,
  *     bounds[*nchunks] = n.
  *   ord_lower / ord_upper (n entries): the rows of each chunk, at the

@@ -310,9 +310,10 @@ namespace bilu {
 // the upper solve in descending order.  The gap of a row r is the distance to
 // its nearest dependency below it, r - max{j < r in L(r)} (and, for U',
 // min{j > r-1 in U(r-1)} - (r-1); the smaller of the two counts).  A cut is
-// placed before the row of largest gap > 1 in [target/2, 2*target] rows (at
+// placed before the row of largest gap > 1 in [target/2, 3*target/2] rows (at
 // most 1024) from the chunk's start, the one nearest to `target` among equal
-// gaps; else at `target`.  In a natural grid ordering the rows of gap > 1
+// gaps; else at `target`.  (Chunks stay within 1.5x the target: every CTA
+// reserves shared memory for the longest one.)  In a natural grid ordering the rows of gap > 1
 // start grid lines and the largest gaps start planes, so chunks hold whole
 // lines and never straddle a plane: the chain along a line never crosses a
 // chunk boundary (a chunk cut inside a line would wait for the previous
@@ -351,7 +352,8 @@ void build_schedule(const bilu_pattern* p, int32_t target, bool upper, bilu_chun
     int32_t hi = (int32_t)std::min<int64_t>(n, (int64_t)lo + target);
     if (hi < n) {
       const int32_t a = lo + std::max(1, target / 2);
-      const int32_t z = (int32_t)std::min<int64_t>({(int64_t)n - 1, (int64_t)lo + 2LL * target, (int64_t)lo + 1024});
+      const int32_t z = (int32_t)std::min<int64_t>({(int64_t)n - 1, (int64_t)lo + target + target / 2,
+                                                    (int64_t)lo + 1024});
       int32_t best = -1;
       int64_t best_gap = 1;
       for (int32_t r = a; r <= z; ++r) {
