@@ -180,6 +180,12 @@ __global__ void __launch_bounds__(kTriWarps * 32) tri_solve_kernel(
       const int i = cur.i;
       TV acc = TV(0);
       bool ok = true;
+      // U': D_i^{-1} y_i depends on no other row: formed before the waits
+      TV z = TV(0);
+      if (UPPER && lane < B) {
+#pragma unroll
+        for (int q = 0; q < B; ++q) z = fma(cur.d[q], (TV)cur.yi[q], z);
+      }
       for (int t0 = cur.beg; t0 < cur.end; t0 += G) {
         const int t = t0 + g;
         if (act && t < cur.end) {
@@ -228,14 +234,7 @@ __global__ void __launch_bounds__(kTriWarps * 32) tri_solve_kernel(
       for (int d = G / 2; d >= 1; d >>= 1) acc += __shfl_down_sync(kFull, acc, d * B);
       double v = 0.0;
       if (lane < B) {
-        if (!UPPER) {
-          v = (double)((TV)cur.own - acc);
-        } else {
-          TV z = TV(0);
-#pragma unroll
-          for (int q = 0; q < B; ++q) z = fma(cur.d[q], (TV)cur.yi[q], z);
-          v = (double)(z - acc);
-        }
+        v = UPPER ? (double)(z - acc) : (double)((TV)cur.own - acc);
         unsigned long long u = (unsigned long long)__double_as_longlong(v);
         if (u == kPending) u = kQuietNaN;
         reinterpret_cast<volatile unsigned long long*>(yl)[(size_t)(i - lo) * B + lane] = u;
