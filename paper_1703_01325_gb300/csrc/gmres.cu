@@ -165,7 +165,10 @@ __global__ void g_fin_step(GState* st, const double* partials, int j, double tol
   const double a = h[j], c = h[j + 1];
   const double rho = sqrt(a * a + c * c);
   st->iters += 1;
-  if (rho == 0.0) {  // w and v_j both vanish: this step adds nothing
+  // rho = 0: w and v_j both vanish, the step adds nothing.  A non-finite
+  // column (an overflowing operator) is dropped the same way: the cycle ends
+  // with the columns before it, so x never takes a non-finite update.
+  if (rho == 0.0 || !isfinite(rho)) {
     st->cols = j;
     st->reason = j == 0 ? gBreakdown : gCycle;
     st->stop = 1;

@@ -208,20 +208,25 @@ __global__ void k_fin(KState* st, const double* partials, int step, int nv, doub
   if (st->stop) return;
   const double bn = sqrt(st->bnorm2);
   switch (step) {
+    // A non-finite scalar (an overflowing operator, e.g. an FP32 preconditioner
+    // on an ill-conditioned system) ends the run as a breakdown before it can
+    // reach x: the kernels that update x run only after the check.
     case kFinAlpha:  // a = (r_hat, v)
-      if (a == 0.0) { st->reason = kBreakdown; st->stop = 1; break; }
+      if (a == 0.0 || !isfinite(a)) { st->reason = kBreakdown; st->stop = 1; break; }
       st->alpha = st->rho / a;
       break;
     case kFinS:  // a = (s, s)
       st->iters += 1;
+      if (!isfinite(a)) { st->reason = kBreakdown; st->stop = 1; break; }
       st->last2 = a;
       if (sqrt(a) / bn <= tol) { st->reason = kConverged; st->stop = 1; }
       break;
     case kFinOmega:  // a = (t, s), c = (t, t)
-      if (c == 0.0) { st->reason = kBreakdown; st->stop = 1; break; }
+      if (c == 0.0 || !isfinite(a) || !isfinite(c)) { st->reason = kBreakdown; st->stop = 1; break; }
       st->omega = a / c;
       break;
     case kFinR:  // a = (r, r), c = (r_hat, r)
+      if (!isfinite(a) || !isfinite(c)) { st->reason = kBreakdown; st->stop = 1; break; }
       st->last2 = a;
       if (sqrt(a) / bn <= tol) { st->reason = kConverged; st->stop = 1; break; }
       if (st->omega == 0.0) { st->reason = kBreakdown; st->stop = 1; break; }
@@ -495,6 +500,7 @@ int run_bicgstab_mixed(const bilu_pattern* p, const bilu_bsr* A, const float* va
     }
     relres = std::sqrt(hn[0]) / std::sqrt(hn[1]);
     if (relres <= tol) { status = BILU_OK; break; }
+    if (!std::isfinite(relres)) { status = BILU_ERR_BREAKDOWN; break; }
     if (iters >= maxit) { status = BILU_ERR_NOT_CONVERGED; break; }
     cudaMemsetAsync(d, 0, (size_t)m * sizeof(double), s);
     int32_t it = 0;

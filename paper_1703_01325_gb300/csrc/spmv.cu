@@ -8,6 +8,10 @@
 // each block column, and the R rows of a warp are consecutive in memory, so
 // every byte of the warp's contiguous value range is used.  Values are
 // streamed with cache-streaming loads; x stays in L2 for the gathers.
+// In FP64 the kernel is bound by the FP64 pipe; in FP32 it is bound by load
+// latency, so the FP32 kernel issues the loads of four blocks (column
+// indices, then values and x) before their FMAs, which run in the same order
+// as one block at a time (identical sums).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -40,7 +44,32 @@ __global__ void __launch_bounds__(256) spmv_kernel(int32_t n, const int32_t* __r
   if (q >= R || row >= n) return;
   const int32_t beg = rp[row], end = rp[row + 1];
   TV acc = TV(0);
-  for (int32_t t = beg; t < end; ++t) {
+  constexpr int U = sizeof(TV) == 4 ? 4 : 1;  // blocks whose loads are in flight together
+  int32_t t = beg;
+  if (U > 1) {
+    for (; t + U <= end; t += U) {
+      int32_t j[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) j[u] = __ldg(ci + t + u);
+      TV av[U][B];
+      double xv[U][B];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const TV* a = vals + (size_t)(t + u) * (B * B) + r;
+#pragma unroll
+        for (int c = 0; c < B; ++c) av[u][c] = ld_stream(a + c * B);
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+#pragma unroll
+        for (int c = 0; c < B; ++c) xv[u][c] = __ldg(x + (size_t)j[u] * B + c);
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+#pragma unroll
+        for (int c = 0; c < B; ++c) acc = fma(av[u][c], (TV)xv[u][c], acc);
+    }
+  }
+  for (; t < end; ++t) {
     const int32_t j = __ldg(ci + t);
     const TV* a = vals + (size_t)t * (B * B) + r;
     const double* xj = x + (size_t)j * B;

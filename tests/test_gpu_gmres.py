@@ -91,3 +91,17 @@ def test_gmres_exact_preconditioner_one_step(B):
     rhs = torch.linspace(1, 2, n * b, dtype=torch.float64, device=DEV)
     x, info = B.gmres_solve(P, A, F, rhs, tol=1e-12, maxit=10)
     assert info.status == 0 and info.iters == 1 and info.true_relres <= 1e-12
+
+
+@pytest.mark.parametrize("solver", ["gmres", "bicgstab"])
+def test_non_finite_operator_is_a_breakdown(B, solver):
+    """A NaN in A makes every Krylov scalar non-finite: both solvers report a
+    breakdown and x keeps its (finite) start value."""
+    S = reservoir_system(6, 5, 4, 3, sigma=1.0, accum=0.01)
+    o, P, F, A, rhs = _setup(B, S, 0)
+    n, b, rp, ci, vals = A
+    bad = vals.clone()
+    bad[5] = float("nan")
+    fn = B.gmres_solve if solver == "gmres" else B.bicgstab_solve
+    x, info = fn(P, (n, b, rp, ci, bad), F, rhs, tol=1e-8, maxit=20)
+    assert info.status == 4 and torch.isfinite(x).all()

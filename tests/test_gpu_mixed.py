@@ -127,3 +127,17 @@ def test_factor_f32_close_to_fp64(B, b, k):
     assert rel_maxerr(Lg, o.L()) <= 1e-4
     assert rel_maxerr(Dg, o.Dinv) <= 1e-4
     assert rel_maxerr(Ug, o.U()) <= 1e-4
+
+
+def test_mixed_overflowing_fp32_copy_is_a_breakdown(B):
+    """A system whose values overflow FP32 (|a| > 3.4e38) has an infinite FP32
+    copy: the refinement reports a breakdown and leaves x finite."""
+    S = reservoir_system(6, 5, 4, 3, sigma=1.0, accum=0.01)
+    rp, ci, vals, rhs = device_system(S, DEV)
+    vals = vals * 1e39
+    P = B.bilu_symbolic(S.n, S.row_ptr, S.col_idx, 0).upload()
+    F, _ = B.bilu_factor(P, 3, vals)
+    F32, vals32 = B.bilu_convert_f32(F), B.bilu_convert_f32(vals)
+    assert not torch.isfinite(vals32).all()
+    x, info = B.bicgstab_solve_mixed(P, (S.n, 3, rp, ci, vals), vals32, F32, rhs, tol=1e-8, maxit=50)
+    assert info.status == 4 and torch.isfinite(x).all()
