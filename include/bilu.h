@@ -367,6 +367,21 @@ int gmres_solve(const bilu_pattern* p, const bilu_bsr* A, const double* d_factor
                 double* d_x, double tol, int32_t maxit, int32_t restart, void* d_work, size_t work_bytes,
                 void* stream, bilu_solve_info* info);
 
+/*
+ * bilu_symbolic_gpu -- the same P', fill levels and Eq. 4 levels as
+ * bilu_symbolic (bit for bit), with the Algorithm 3 row merges run on the
+ * current device: one warp per row, rows in ascending order, row i waiting
+ * (bounded) for each pivot row p < i it merges.  Inputs are host arrays as for
+ * bilu_symbolic; the returned handle is the same kind (not yet uploaded).
+ *   row_capacity in [1, 8192]: the most entries any row of P' may hold; a row
+ *   that outgrows it returns BILU_ERR_OOM (retry with a larger capacity).
+ *   Device scratch of about 8 * n * row_capacity bytes is allocated and freed
+ *   inside the call; the stream is synchronised.  BILU_ERR_TIMEOUT if a wait
+ *   exceeds the spin limit (bilu_set_spin_limit_ns).
+ */
+int bilu_symbolic_gpu(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, int32_t k, int32_t row_capacity,
+                      void* stream, bilu_pattern** out);
+
 /* ---- adjoint: A^T lambda = g with the transposed factors ----
  *
  * A loss L(x) through x = A^{-1} b has dL/db = lambda and dL/dA_IJ =

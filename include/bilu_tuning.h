@@ -83,7 +83,8 @@ enum bilu_prof_kernel {
   BILU_PROF_KRYLOV = 7,       /* BiCGSTAB vector updates and reductions */
   BILU_PROF_FACTOR_INIT = 8,  /* factor: reset of the ready flags */
   BILU_PROF_ADJOINT = 9,      /* adjoint: block gather-transposes and -lambda x^T */
-  BILU_PROF_NKERNELS = 10
+  BILU_PROF_SYMBOLIC = 10,    /* device symbolic phase (bilu_symbolic_gpu) */
+  BILU_PROF_NKERNELS = 11
 };
 
 /* Per-kernel timing: when on, every launch of the library is bracketed by

@@ -87,6 +87,7 @@ SIGNATURES = {
     "gmres_workspace_bytes": (C.c_size_t, [_vp, C.c_int32, C.c_int32]),
     "gmres_solve": (C.c_int, [_vp, C.POINTER(BSR), _vp, _vp, _vp, C.c_double, C.c_int32, C.c_int32, _vp,
                               C.c_size_t, _vp, C.POINTER(SolveInfo)]),
+    "bilu_symbolic_gpu": (C.c_int, [C.c_int32, _i32p, _i32p, C.c_int32, C.c_int32, _vp, C.POINTER(_vp)]),
     "bilu_pattern_transpose": (C.c_int, [_vp, C.POINTER(_vp)]),
     "bilu_factor_transpose": (C.c_int, [_vp, C.c_int32, _vp, _vp, _vp]),
     "bsr_transpose_pattern": (C.c_int, [C.c_int32, _i32p, _i32p, _i32p, _i32p, _i32p]),
@@ -95,7 +96,7 @@ SIGNATURES = {
 }
 
 PROF_KERNELS = ["spmv", "apply_prep", "lower_solve", "upper_solve", "backfill", "factor",
-                "scale_upper", "krylov_vector", "factor_init", "adjoint"]
+                "scale_upper", "krylov_vector", "factor_init", "adjoint", "symbolic"]
 
 _lib = None
 

@@ -154,6 +154,20 @@ def bilu_symbolic(n: int, row_ptr, col_idx, k: int) -> Pattern:
     return Pattern(h)
 
 
+def bilu_symbolic_gpu(n: int, row_ptr, col_idx, k: int, row_capacity: int = 256, stream=None) -> Pattern:
+    """The same pattern as bilu_symbolic, with Algorithm 3's row merges run on
+    the current CUDA device (bilu_symbolic_gpu)."""
+    rp = _host_i32(row_ptr)
+    ci = _host_i32(col_idx)
+    if len(rp) != n + 1:
+        raise ValueError("row_ptr must hold n + 1 entries")
+    h = C.c_void_p()
+    p = lambda a: a.ctypes.data_as(C.POINTER(C.c_int32))
+    _check(L.load().bilu_symbolic_gpu(n, p(rp), p(ci) if len(ci) else None, k, row_capacity,
+                                      _stream_handle(stream), C.byref(h)), "bilu_symbolic_gpu")
+    return Pattern(h)
+
+
 def workspace(nbytes: int, device=None) -> torch.Tensor:
     """A device scratch buffer of at least nbytes bytes (torch allocation)."""
     return torch.empty(max(int(nbytes), 256), dtype=torch.uint8,

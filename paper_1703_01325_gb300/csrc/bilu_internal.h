@@ -129,6 +129,9 @@ size_t apply_workspace_bytes(int32_t n, int32_t b);
 int ensure_schedule(const bilu_pattern* p, bilu_chunk_schedule* s, int32_t chunk, bool upper);
 // Host part (symbolic.cpp).
 void build_schedule(const bilu_pattern* p, int32_t chunk, bool upper, bilu_chunk_schedule* s);
+// Eq. 4 levels, L / U' split and backfill map of a pattern with rp, ci, lev set.
+int complete_pattern(bilu_pattern* p, const int32_t* row_ptr, const int32_t* col_idx);
+int validate_pattern(int32_t n, const int32_t* row_ptr, const int32_t* col_idx);
 void free_schedule(bilu_chunk_schedule* s);
 int launch_apply(const bilu_pattern* p, int32_t b, const double* f, const double* r, double* x,
                  void* work, int32_t* stop, void* stream);

@@ -96,6 +96,45 @@ void finish_pattern(bilu_pattern* p) {
 
 }  // namespace
 
+namespace bilu {
+
+// Eq. 4 levels, the L / U' split and the backfill gather map (Algorithm 5
+// steps 3-4: slot -> A block or -1) of a pattern whose n, k, nnz_a, rp, ci and
+// lev are set (by the host symbolic phase or the device one).
+int complete_pattern(bilu_pattern* p, const int32_t* row_ptr, const int32_t* col_idx) {
+  const int32_t n = p->n;
+  finish_pattern(p);
+  const int64_t nl = p->nnz_l(), nslots = p->nslots();
+  if (nslots > (int64_t)INT32_MAX) return BILU_ERR_OOM;
+  p->slot_src.assign((size_t)nslots, -1);
+  for (int32_t i = 0; i < n; ++i) {
+    int32_t a = p->lrp[i], c = p->urp[i];
+    for (int32_t t = row_ptr[i]; t < row_ptr[i + 1]; ++t) {
+      const int32_t j = col_idx[t];
+      int64_t slot;
+      if (j < i) {
+        while (p->lci[a] != j) ++a;  // A's pattern is a subset of P'
+        slot = a;
+      } else if (j == i) {
+        slot = nl + i;
+      } else {
+        while (p->uci[c] != j) ++c;
+        slot = nl + n + c;
+      }
+      p->slot_src[(size_t)slot] = t;
+    }
+  }
+  return BILU_OK;
+}
+
+// The block CSR checks of bilu_symbolic (sorted, unique, in range, diagonal
+// present), for the device symbolic phase.
+int validate_pattern(int32_t n, const int32_t* row_ptr, const int32_t* col_idx) {
+  return check_pattern(n, row_ptr, col_idx);
+}
+
+}  // namespace bilu
+
 extern "C" int bilu_symbolic(int32_t n, const int32_t* row_ptr, const int32_t* col_idx, int32_t k,
                              bilu_pattern** out) {
   if (!out || k < 0) return BILU_ERR_ARG;
@@ -158,31 +197,9 @@ extern "C" int bilu_symbolic(int32_t n, const int32_t* row_ptr, const int32_t* c
       p->rp[(size_t)i + 1] = (int32_t)p->ci.size();
     }
 
-    finish_pattern(p);
-
-    // Backfill gather map (Algorithm 5 steps 3-4): slot -> A block or -1.
-    const int64_t nl = p->nnz_l(), nslots = p->nslots();
-    if (nslots > (int64_t)INT32_MAX) {
+    if (bilu::complete_pattern(p, row_ptr, col_idx) != BILU_OK) {
       delete p;
       return BILU_ERR_OOM;
-    }
-    p->slot_src.assign((size_t)nslots, -1);
-    for (int32_t i = 0; i < n; ++i) {
-      int32_t a = p->lrp[i], c = p->urp[i];
-      for (int32_t t = row_ptr[i]; t < row_ptr[i + 1]; ++t) {
-        const int32_t j = col_idx[t];
-        int64_t slot;
-        if (j < i) {
-          while (p->lci[a] != j) ++a;  // A's pattern is a subset of P'
-          slot = a;
-        } else if (j == i) {
-          slot = nl + i;
-        } else {
-          while (p->uci[c] != j) ++c;
-          slot = nl + n + c;
-        }
-        p->slot_src[(size_t)slot] = t;
-      }
     }
   } catch (const std::bad_alloc&) {
     delete p;
