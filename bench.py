@@ -251,13 +251,16 @@ def ms_to_tol_small(B, dev, stream, reps=5):
 
 
 def precision_compare(B, dev, stream, cases=((2, 1), (4, 1)), tol=1e-8):
-    """FP32-stored preconditioner and FP32 SpMV inside FP64 iterative
-    refinement (bilu_factor_f32 + bicgstab_solve_mixed) against the plain
-    FP64 solve (bilu_factor + bicgstab_solve), both from x0 = 0 to a true
-    relative residual of `tol`, on the 96 x 96 x 48 7-point workload at block
-    sizes b and fill levels k.  Times include the factorization.  The mixed
-    solution's distance to the FP64 one (which the parity tests hold to the
-    CPU oracle) is reported as its error."""
+    """Two FP32-preconditioner solvers against the plain FP64 solve
+    (bilu_factor + bicgstab_solve), all from x0 = 0 to a true relative
+    residual of `tol`, on the 96 x 96 x 48 7-point workload at block sizes b
+    and fill levels k: "mixed" = FP32-stored preconditioner and FP32 SpMV
+    inside FP64 iterative refinement (bilu_factor_f32 + bicgstab_solve_mixed);
+    "f32prec" = FP64 BiCGSTAB with the FP32-stored preconditioner
+    (bilu_factor_f32 + bicgstab_solve_f32prec); "f32prec_from_fp64" = the same
+    with the FP64 factors rounded to FP32 (bilu_factor + bilu_convert_f32).
+    Times include the factorization.  Each solution's distance to the FP64 one (which the parity
+    tests hold to the CPU oracle) is reported as its error."""
     import torch
     from paper_1703_01325_gb300.reservoir import WORKLOADS, reservoir_system
     out = []
@@ -287,8 +290,21 @@ def precision_compare(B, dev, stream, cases=((2, 1), (4, 1)), tol=1e-8):
             return B.bicgstab_solve_mixed(P, A, vals32, F32, rhs, x=x32, tol=tol, maxit=5000, inner_tol=1e-3,
                                           inner_maxit=300, work=mw)[1]
 
+        def f32prec():
+            B.bilu_factor_f32(P, b, vals, F32, fw)
+            xp.zero_()
+            return B.bicgstab_solve_f32prec(P, A, F32, rhs, x=xp, tol=tol, maxit=5000, work=sw)[1]
+
+        def f32prec_from_fp64():
+            B.bilu_factor(P, b, vals, F, fw)
+            B.bilu_convert_f32(F, F32)
+            xq.zero_()
+            return B.bicgstab_solve_f32prec(P, A, F32, rhs, x=xq, tol=tol, maxit=5000, work=sw)[1]
+
+        xp, xq = torch.zeros_like(rhs), torch.zeros_like(rhs)
         row = {"workload": "grid96x96x48_7pt", "b": b, "k": k}
-        for name, fn in (("fp64", fp64), ("mixed", mixed)):
+        for name, fn in (("fp64", fp64), ("mixed", mixed), ("f32prec", f32prec),
+                         ("f32prec_from_fp64", f32prec_from_fp64)):
             fn()  # warm-up
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             torch.cuda.synchronize()
@@ -300,6 +316,10 @@ def precision_compare(B, dev, stream, cases=((2, 1), (4, 1)), tol=1e-8):
                          "status": si.status}
         row["mixed_x_rel_err_vs_fp64"] = float((x32 - x64).norm() / x64.norm())
         row["mixed_speedup"] = round(row["fp64"]["ms"] / row["mixed"]["ms"], 3)
+        row["f32prec_x_rel_err_vs_fp64"] = float((xp - x64).norm() / x64.norm())
+        row["f32prec_speedup"] = round(row["fp64"]["ms"] / row["f32prec"]["ms"], 3)
+        row["f32prec_from_fp64_x_rel_err_vs_fp64"] = float((xq - x64).norm() / x64.norm())
+        row["f32prec_from_fp64_speedup"] = round(row["fp64"]["ms"] / row["f32prec_from_fp64"]["ms"], 3)
         out.append(row)
         P.close()
     return out

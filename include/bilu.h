@@ -343,6 +343,19 @@ int bicgstab_solve_mixed(const bilu_pattern* p, const bilu_bsr* A, const float* 
                          int32_t maxit, double inner_tol, int32_t inner_maxit, void* d_work,
                          size_t work_bytes, void* stream, bilu_solve_info* info);
 
+/*
+ * bicgstab_solve_f32prec -- the BiCGSTAB of bicgstab_solve (FP64 SpMV with
+ * A->vals, FP64 vectors, scalars, dot products and true residual) with the
+ * preconditioner stored and applied in FP32 (d_factors32 from
+ * bilu_factor_f32 or bilu_convert_f32).  One Krylov space, no restarts: the
+ * FP32 preconditioner changes only how fast the FP64 iteration converges,
+ * not the accuracy it reaches.  Workspace: bicgstab_workspace_bytes.  Other
+ * arguments and results as for bicgstab_solve.
+ */
+int bicgstab_solve_f32prec(const bilu_pattern* p, const bilu_bsr* A, const float* d_factors32, const double* d_rhs,
+                           double* d_x, double tol, int32_t maxit, void* d_work, size_t work_bytes, void* stream,
+                           bilu_solve_info* info);
+
 /* Scratch bytes gmres_solve needs for restart length `restart` (0 for invalid
  * arguments). */
 size_t gmres_workspace_bytes(const bilu_pattern* p, int32_t b, int32_t restart);

@@ -84,6 +84,8 @@ SIGNATURES = {
     "bilu_profile_read": (C.c_int, [C.c_int32, C.POINTER(C.c_int64), C.POINTER(C.c_double)]),
     "bilu_launch_count": (C.c_int64, []),
     "bilu_schedule_export": (C.c_int, [_vp, C.c_int32, _i32p, _i32p, _i32p, _i32p, _i32p, _i32p]),
+    "bicgstab_solve_f32prec": (C.c_int, [_vp, C.POINTER(BSR), _vp, _vp, _vp, C.c_double, C.c_int32, _vp,
+                                         C.c_size_t, _vp, C.POINTER(SolveInfo)]),
     "gmres_workspace_bytes": (C.c_size_t, [_vp, C.c_int32, C.c_int32]),
     "gmres_solve": (C.c_int, [_vp, C.POINTER(BSR), _vp, _vp, _vp, C.c_double, C.c_int32, C.c_int32, _vp,
                               C.c_size_t, _vp, C.POINTER(SolveInfo)]),

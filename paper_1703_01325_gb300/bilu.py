@@ -266,6 +266,27 @@ def bicgstab_solve(pattern: Pattern, A, factors: torch.Tensor, rhs: torch.Tensor
     return x, info
 
 
+def bicgstab_solve_f32prec(pattern: Pattern, A, factors32: torch.Tensor, rhs: torch.Tensor,
+                           x: torch.Tensor | None = None, tol: float = 1e-8, maxit: int = 1000,
+                           work: torch.Tensor | None = None, stream=None):
+    """FP64 BiCGSTAB with the FP32-stored preconditioner (bicgstab_solve_f32prec)."""
+    n, b, rp, ci, vals = A
+    if x is None:
+        x = torch.zeros_like(rhs)
+    if work is None:
+        work = workspace(pattern.bicgstab_workspace_bytes(b), rhs.device)
+    bsr = L.BSR(n, b, _dev(rp, torch.int32, "row_ptr"), _dev(ci, torch.int32, "col_idx"),
+                _dev(vals, torch.float64, "vals"))
+    info = L.SolveInfo()
+    st = L.load().bicgstab_solve_f32prec(pattern.handle, C.byref(bsr), _dev(factors32, torch.float32, "factors32"),
+                                         _dev(rhs, torch.float64, "rhs"), _dev(x, torch.float64, "x"), tol, maxit,
+                                         _dev(work, torch.uint8, "work"), work.numel(), _stream_handle(stream),
+                                         C.byref(info))
+    if st in (L.BILU_ERR_ARG, L.BILU_ERR_STATE, L.BILU_ERR_CUDA, L.BILU_ERR_OOM):
+        _check(st, "bicgstab_solve_f32prec")
+    return x, info
+
+
 def gmres_solve(pattern: Pattern, A, factors: torch.Tensor, rhs: torch.Tensor, x: torch.Tensor | None = None,
                 tol: float = 1e-8, maxit: int = 1000, restart: int = 20, work: torch.Tensor | None = None,
                 stream=None):

@@ -254,6 +254,30 @@ extern "C" int bicgstab_solve(const bilu_pattern* p, const bilu_bsr* A, const do
   return run_bicgstab(p, A, d_factors, d_rhs, d_x, tol, maxit, d_work, stream, info, g_check_every);
 }
 
+extern "C" int bicgstab_solve_f32prec(const bilu_pattern* p, const bilu_bsr* A, const float* d_factors32,
+                                      const double* d_rhs, double* d_x, double tol, int32_t maxit, void* d_work,
+                                      size_t work_bytes, void* stream, bilu_solve_info* info) {
+  if (info) {
+    info->status = BILU_ERR_ARG;
+    info->iters = 0;
+    info->true_relres = 0.0;
+    info->ms = 0.0;
+  }
+  if (!p || !A || !valid_b(A->b) || A->n != p->n || !(tol > 0.0) || maxit < 0) return BILU_ERR_ARG;
+  int st = ready(p);
+  if (st) return st;
+  if (p->n == 0) {
+    if (info) info->status = BILU_OK;
+    return BILU_OK;
+  }
+  if (!A->row_ptr || !A->col_idx || !A->vals || !d_factors32 || !d_rhs || !d_x || !d_work ||
+      (const void*)d_rhs == (const void*)d_x)
+    return BILU_ERR_ARG;
+  if (work_bytes < krylov_workspace_bytes(p->n, A->b)) return BILU_ERR_STATE;
+  if (solve_schedule(p) != 0) return BILU_ERR_OOM;
+  return run_bicgstab(p, A, nullptr, d_rhs, d_x, tol, maxit, d_work, stream, info, g_check_every, d_factors32);
+}
+
 extern "C" size_t gmres_workspace_bytes(const bilu_pattern* p, int32_t b, int32_t restart) {
   if (!p || !valid_b(b) || restart < 1 || restart > gmres_max_restart()) return 0;
   return gmres_workspace_bytes_impl(p->n, b, restart);

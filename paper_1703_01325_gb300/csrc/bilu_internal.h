@@ -163,6 +163,6 @@ int run_gmres(const bilu_pattern* p, const bilu_bsr* A, const double* f, const d
               int32_t maxit, int32_t m, void* work, void* stream, bilu_solve_info* info, int batch);
 int run_bicgstab(const bilu_pattern* p, const bilu_bsr* A, const double* f, const double* rhs,
                  double* x, double tol, int32_t maxit, void* work, void* stream,
-                 bilu_solve_info* info, int batch);
+                 bilu_solve_info* info, int batch, const float* f32 = nullptr);
 
 }  // namespace bilu

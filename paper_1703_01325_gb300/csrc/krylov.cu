@@ -427,17 +427,24 @@ struct Timer {
 
 }  // namespace
 
+// FP64 BiCGSTAB (FP64 SpMV, vectors, scalars and dot products) with the
+// preconditioner stored and applied in double (f) or in float (f32).
 int run_bicgstab(const bilu_pattern* p, const bilu_bsr* A, const double* f, const double* rhs,
                  double* x, double tol, int32_t maxit, void* work, void* stream,
-                 bilu_solve_info* info, int batch) {
+                 bilu_solve_info* info, int batch, const float* f32) {
   const int32_t n = p->n, b = A->b;
   KOps ops;
   ops.spmv = [=](const double* xin, double* yout, int32_t* stop, void*) {
     return launch_spmv(n, b, A->row_ptr, A->col_idx, A->vals, xin, yout, stream, stop);
   };
-  ops.apply = [=](const double* rin, double* zout, int32_t* stop, void* aw) {
-    return launch_apply(p, b, f, rin, zout, aw, stop, stream);
-  };
+  if (f32)
+    ops.apply = [=](const double* rin, double* zout, int32_t* stop, void* aw) {
+      return launch_apply_f32(p, b, f32, rin, zout, aw, stop, stream);
+    };
+  else
+    ops.apply = [=](const double* rin, double* zout, int32_t* stop, void* aw) {
+      return launch_apply(p, b, f, rin, zout, aw, stop, stream);
+    };
   Timer timer((cudaStream_t)stream);
   int32_t iters = 0;
   double relres = 0.0;

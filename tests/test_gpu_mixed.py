@@ -141,3 +141,27 @@ def test_mixed_overflowing_fp32_copy_is_a_breakdown(B):
     assert not torch.isfinite(vals32).all()
     x, info = B.bicgstab_solve_mixed(P, (S.n, 3, rp, ci, vals), vals32, F32, rhs, tol=1e-8, maxit=50)
     assert info.status == 4 and torch.isfinite(x).all()
+
+
+@pytest.mark.parametrize("k", [0, 1])
+def test_bicgstab_f32prec_reaches_fp64_accuracy(B, k):
+    """FP64 BiCGSTAB with the FP32-stored preconditioner reaches the FP64
+    tolerance, its solution matches the oracle's FP64 solve, and it needs
+    about as many iterations as the FP64 preconditioner."""
+    S = reservoir_system(16, 16, 8, 3, sigma=1.0, accum=0.01)
+    o = OracleRun(S.n, 3, S.row_ptr, S.col_idx, S.vals, k)
+    rp, ci, vals, rhs = device_system(S, DEV)
+    P = B.bilu_symbolic(S.n, S.row_ptr, S.col_idx, k).upload()
+    F32, _ = B.bilu_factor_f32(P, 3, vals)
+    F, _ = B.bilu_factor(P, 3, vals)
+    A = (S.n, 3, rp, ci, vals)
+    x, info = B.bicgstab_solve_f32prec(P, A, F32, rhs, tol=1e-10, maxit=2000)
+    assert info.status == 0 and info.true_relres <= 1e-10
+    _, info64 = B.bicgstab_solve(P, A, F, rhs, tol=1e-10, maxit=2000)
+    assert info.iters <= 1.5 * info64.iters + 2
+    xg = x.cpu().numpy()
+    res = np.linalg.norm(S.rhs - o.spmv(xg)) / np.linalg.norm(S.rhs)
+    assert res <= 1e-10 * (1 + 1e-6)
+    xo, _, _, st = oracle.bicgstab(S.n, 3, S.row_ptr, S.col_idx, S.vals, o.prp, o.pci, o.F, o.Dinv, S.rhs,
+                                   tol=1e-12, maxit=2000)
+    assert st == 0 and np.linalg.norm(xg - xo) <= 1e-7 * np.linalg.norm(xo)
