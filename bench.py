@@ -176,10 +176,35 @@ def cpu_baseline(S, k, gpu_iters, sample_iters=4):
     per_it = (t3 - t2) / sample_iters
     factor_ms = (t2 - t1) * 1e3
     value = factor_ms + per_it * 1e3 * max(gpu_iters, 1)
+    t4 = time.perf_counter()
+    oracle.spmv(S.n, S.b, S.row_ptr, S.col_idx, S.vals, S.rhs)
+    t5 = time.perf_counter()
+    oracle.apply(S.n, S.b, prp, pci, F, D, S.rhs)
+    t6 = time.perf_counter()
     return {"value": round(value, 1), "unit": "ms", "cores": 1, "kind": "oracle",
+            "cpu_model": cpu_model(), "nproc": os.cpu_count(),
+            "kernels_ms": {"symbolic": round(1e3 * (t1 - t0), 1), "factor": round(factor_ms, 1),
+                           "spmv": round(1e3 * (t5 - t4), 1), "apply": round(1e3 * (t6 - t5), 1)},
             "sample": (f"oracle factorization of the full matrix ({factor_ms:.0f} ms) + {sample_iters} "
                        f"BiCGSTAB iterations ({per_it * 1e3:.0f} ms each), scaled to {gpu_iters} iterations; "
                        f"symbolic {1e3 * (t1 - t0):.0f} ms not counted")}
+
+
+def cpu_model() -> str:
+    """The host CPU's model name (as /proc/cpuinfo or lscpu give it)."""
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith(("model name", "cpu model")):
+                    return line.split(":", 1)[1].strip()
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
 
 
 def run_reference(args):
@@ -214,6 +239,7 @@ def run_reference(args):
         "config": {"workload": args.workload, "k": args.k, "tol": args.tol, "maxit": args.maxit, **cfg,
                    "step": "backfill + factor + BiCGSTAB iterations up to maxit"},
         "cpu_baseline": {"value": round(ms, 1), "unit": "ms", "cores": 1, "kind": "oracle",
+                         "cpu_model": cpu_model(), "nproc": os.cpu_count(),
                          "sample": f"per step: full factorization + {sample_iters} BiCGSTAB iterations, "
                                    f"scaled to {iters_ref} iterations"},
         "e2e": {"value": round(ms, 1), "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},

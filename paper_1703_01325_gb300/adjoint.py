@@ -31,7 +31,7 @@ class BlockILUSolver:
     on the pattern only).
     """
 
-    def __init__(self, n: int, b: int, row_ptr, col_idx, k: int, tol: float = 1e-12, maxit: int = 5000,
+    def __init__(self, n: int, b: int, row_ptr, col_idx, k: int, tol: float = 1e-10, maxit: int = 5000,
                  device="cuda"):
         self.n, self.b, self.k = n, b, k
         self.tol, self.maxit = tol, maxit
