@@ -66,6 +66,9 @@ __global__ void apply_prep_kernel(double* y, long long m, int32_t* header, const
   }
 }
 
+template <typename TV>
+constexpr bool kFoldOwn = sizeof(TV) == 8;  // see fetch_deps
+
 // Registers a lane holds for one row: the row, its first block of this lane's
 // group (column, this lane's B values, optimistic dependency values), and what
 // the row's own update needs (r_i for L; D_i^{-1} row and y_i for U').
@@ -74,9 +77,9 @@ struct RowPre {
   int i, beg, end, j;
   TV av[B];
   unsigned long long yv[B];  // dependency values of a block outside the chunk, read early
-  double own;                // L: r_i[lane]
-  TV d[B];                   // U': D_i^{-1}[lane][q]
-  double yi[B];              // U': y_i[q]
+  double own;                // L: r_i[lane]; U': (D_i^{-1} y_i)[lane] once folded
+  TV d[B];                   // U': D_i^{-1}[lane][q]  (until folded into own)
+  double yi[B];              // U': y_i[q]             (until folded into own)
 };
 
 // Stage A of the prefetch: the row, its first block (column and values) and
@@ -120,11 +123,22 @@ __device__ __forceinline__ void fetch_row(RowPre<B, UPPER, TV>& p, int pos, int 
 
 // Stage B: a dependency outside the chunk is usually final already: read it
 // now (relaxed); if it still holds the pending pattern it is waited for later.
+// For U' the row's own term D_i^{-1} y_i depends on no other row.  In FP64 it
+// is folded into `own` here, a turn after its operands were loaded, so that
+// neither the operands (registers) nor the FP64 product stay on the row's
+// critical path (measured: 3 % faster in FP64, 3 % slower in FP32, where the
+// product is cheap and is formed at the start of the row instead).
 template <int B, bool UPPER, typename TV>
-__device__ __forceinline__ void fetch_deps(RowPre<B, UPPER, TV>& p, const double* out, int lo, int hi) {
+__device__ __forceinline__ void fetch_deps(RowPre<B, UPPER, TV>& p, const double* out, int lo, int hi, int lane) {
   const bool remote = p.j >= 0 && (p.j < lo || p.j >= hi);
 #pragma unroll
   for (int q = 0; q < B; ++q) p.yv[q] = remote ? ld_relaxed_u64(out + (size_t)p.j * B + q) : kPending;
+  if (UPPER && kFoldOwn<TV> && lane < B) {
+    TV z = TV(0);
+#pragma unroll
+    for (int q = 0; q < B; ++q) z = fma(p.d[q], (TV)p.yi[q], z);
+    p.own = (double)z;
+  }
 }
 
 template <int B, bool UPPER, typename TV, int kTriWarps>
@@ -170,21 +184,25 @@ __global__ void __launch_bounds__(kTriWarps * 32) tri_solve_kernel(
     __syncthreads();
     RowPre<B, UPPER, TV> cur, nx1, nx2;
     fetch_row<B, UPPER, TV>(cur, warp, len, s_i, s_beg, s_end, ci, vals, dinv, rhs, g, rr, act, lane);
-    fetch_deps<B, UPPER, TV>(cur, out, lo, hi);
+    fetch_deps<B, UPPER, TV>(cur, out, lo, hi, lane);
     fetch_row<B, UPPER, TV>(nx1, warp + kTriWarps, len, s_i, s_beg, s_end, ci, vals, dinv, rhs, g, rr, act,
                             lane);
     for (int pos = warp; pos < len && !dead; pos += kTriWarps) {
       fetch_row<B, UPPER, TV>(nx2, pos + 2 * kTriWarps, len, s_i, s_beg, s_end, ci, vals, dinv, rhs, g, rr,
                               act, lane);
-      fetch_deps<B, UPPER, TV>(nx1, out, lo, hi);
+      fetch_deps<B, UPPER, TV>(nx1, out, lo, hi, lane);
       const int i = cur.i;
       TV acc = TV(0);
       bool ok = true;
-      // U': D_i^{-1} y_i depends on no other row: formed before the waits
-      TV z = TV(0);
-      if (UPPER && lane < B) {
+      // the row's own term in TV, formed before the waits (FP32 U': D_i^{-1} y_i here)
+      TV own = TV(0);
+      if (lane < B) {
+        if (UPPER && !kFoldOwn<TV>) {
 #pragma unroll
-        for (int q = 0; q < B; ++q) z = fma(cur.d[q], (TV)cur.yi[q], z);
+          for (int q = 0; q < B; ++q) own = fma(cur.d[q], (TV)cur.yi[q], own);
+        } else {
+          own = (TV)cur.own;
+        }
       }
       for (int t0 = cur.beg; t0 < cur.end; t0 += G) {
         const int t = t0 + g;
@@ -234,7 +252,7 @@ __global__ void __launch_bounds__(kTriWarps * 32) tri_solve_kernel(
       for (int d = G / 2; d >= 1; d >>= 1) acc += __shfl_down_sync(kFull, acc, d * B);
       double v = 0.0;
       if (lane < B) {
-        v = UPPER ? (double)(z - acc) : (double)((TV)cur.own - acc);
+        v = (double)(own - acc);
         unsigned long long u = (unsigned long long)__double_as_longlong(v);
         if (u == kPending) u = kQuietNaN;
         reinterpret_cast<volatile unsigned long long*>(yl)[(size_t)(i - lo) * B + lane] = u;
