@@ -43,7 +43,7 @@ extern "C" const char* bilu_status_string(int status) {
     case BILU_ERR_ARG: return "invalid argument";
     case BILU_ERR_PATTERN: return "malformed block pattern (unsorted, duplicate or out-of-range column, or missing diagonal block)";
     case BILU_ERR_SINGULAR: return "singular or non-finite pivot block";
-    case BILU_ERR_BREAKDOWN: return "BiCGSTAB breakdown";
+    case BILU_ERR_BREAKDOWN: return "Krylov breakdown (a zero or non-finite scalar)";
     case BILU_ERR_NOT_CONVERGED: return "iteration limit reached before the tolerance";
     case BILU_ERR_TIMEOUT: return "a bounded dependency wait timed out";
     case BILU_ERR_CUDA: return "CUDA runtime error";
@@ -61,6 +61,9 @@ extern "C" int bilu_pattern_upload(bilu_pattern* p, void* stream) {
     cudaFree(p->d_mem);
     p->d_mem = nullptr;
   }
+  // the schedules live on the device of the previous upload: rebuild them here
+  free_schedule(&p->solve);
+  free_schedule(&p->fact);
   const int32_t n = p->n;
   if (n == 0) {
     p->device = dev;
