@@ -207,6 +207,31 @@ def cpu_model() -> str:
     return platform.processor() or platform.machine()
 
 
+def replica_group(backend: str, device=None):
+    """(dist, world, rank, local) from the launcher's environment.  With more
+    than one rank every rank solves its own copy of the workload (replicas:
+    the ILU(k) recurrences do not shard), so the group only times them."""
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world <= 1:
+        return None, 1, 0, local
+    import torch.distributed as dist
+    kw = {"device_id": device} if device is not None else {}
+    dist.init_process_group(backend, **kw)
+    return dist, world, rank, local
+
+
+def max_over_ranks(value: float, dist, device="cpu") -> float:
+    """The largest value over all ranks (the slowest replica's step time)."""
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def run_reference(args):
     """Reference arm: the CPU oracle as it stands, on the same workload."""
     rank = int(os.environ.get("RANK", "0"))
@@ -390,13 +415,8 @@ def main():
     import paper_1703_01325_gb300.bilu as B
     from paper_1703_01325_gb300 import _lib as L
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
-    dist = None
-    if world > 1:  # independent replicas: the method does not shard (one system per GPU)
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=torch.device(f"cuda:{local}"))
+    dist, world, rank, local = replica_group("nccl", torch.device(f"cuda:{local}"))
     dev = torch.device(f"cuda:{local}")
     torch.cuda.set_device(dev)
     lib = L.load()
@@ -453,9 +473,7 @@ def main():
         prof[name] = (nl.value, tm.value)
     lib.bilu_profile_enable(0)
     if dist:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+        ms = max_over_ranks(ms, dist, dev)
 
     ab = algorithmic_bytes(S.n, b, S.nnzb, info.nnz_l, info.nnz_u)
     hbm, peak_src = peaks()
