@@ -80,6 +80,7 @@ enum HeaderWord : int {
 constexpr size_t kHeaderBytes = kHeaderWords * 4;
 
 inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+inline size_t align_up16(size_t x) { return (x + 15) & ~(size_t)15; }
 
 // Default spin limit of a dependency wait, in nanoseconds of %globaltimer.
 constexpr long long kDefaultSpinNs = 2000000000LL;  // 2 s

@@ -107,24 +107,45 @@ __device__ __forceinline__ bool wait_values(const double* p, double (&out)[N], W
   }
 }
 
-// Wait until all N values in this CTA's shared memory at p hold computed
-// values (volatile 64-bit loads: each value is its own ready flag, so no
+// Bit patterns of a value type for the shared-memory value cache of the
+// solves: "pending" is a signalling NaN with a fixed payload (no arithmetic
+// produces one), "quiet" replaces a computed value that would collide.
+template <typename TV>
+struct ValueBits;
+template <>
+struct ValueBits<double> {
+  using U = unsigned long long;
+  static constexpr U kPend = kPending, kQuiet = kQuietNaN;
+  __device__ static U bits(double v) { return (U)__double_as_longlong(v); }
+  __device__ static double value(U u) { return __longlong_as_double((long long)u); }
+};
+template <>
+struct ValueBits<float> {
+  using U = unsigned int;
+  static constexpr U kPend = 0x7FA5A5A5u, kQuiet = 0x7FC00000u;
+  __device__ static U bits(float v) { return (U)__float_as_uint(v); }
+  __device__ static float value(U u) { return __uint_as_float(u); }
+};
+
+// Wait until all N values of type TV in this CTA's shared memory at p hold
+// computed values (volatile loads: each value is its own ready flag, so no
 // fence is needed); false if the wait was abandoned.  The abort word and the
 // clock are consulted only every 1024 polls: a shared-memory poll is short.
-template <int N>
-__device__ __forceinline__ bool wait_values_shared(const double* p, double (&out)[N], Waiter& w) {
+template <int N, typename TV>
+__device__ __forceinline__ bool wait_values_shared(const TV* p, TV (&out)[N], Waiter& w) {
+  using VB = ValueBits<TV>;
   w.t0 = 0;
-  const volatile unsigned long long* v = reinterpret_cast<const volatile unsigned long long*>(p);
+  const volatile typename VB::U* v = reinterpret_cast<const volatile typename VB::U*>(p);
   for (unsigned it = 1;; ++it) {
-    unsigned long long u[N];
+    typename VB::U u[N];
 #pragma unroll
     for (int q = 0; q < N; ++q) u[q] = v[q];
     bool all = true;
 #pragma unroll
-    for (int q = 0; q < N; ++q) all = all && (u[q] != kPending);
+    for (int q = 0; q < N; ++q) all = all && (u[q] != VB::kPend);
     if (all) {
 #pragma unroll
-      for (int q = 0; q < N; ++q) out[q] = __longlong_as_double((long long)u[q]);
+      for (int q = 0; q < N; ++q) out[q] = VB::value(u[q]);
       return true;
     }
     if (w.give_up(it, 1023u)) return false;

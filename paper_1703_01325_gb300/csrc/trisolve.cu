@@ -52,12 +52,15 @@ TrisolveConfig& trisolve_config() {
 namespace {
 
 
-__global__ void apply_prep_kernel(double* y, long long m, int32_t* header, const int32_t* stop) {
-  // Each apply starts with a clean header: its status is its own.
+__global__ void apply_prep_kernel(double* y, double* x, long long m, int32_t* header, const int32_t* stop) {
+  // Each apply starts with a clean header: its status is its own.  Both
+  // solves' outputs start "pending".
   if (stop && *stop) return;
   const long long stride = (long long)gridDim.x * blockDim.x;
-  for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < m; q += stride)
+  for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < m; q += stride) {
     reinterpret_cast<unsigned long long*>(y)[q] = kPending;
+    reinterpret_cast<unsigned long long*>(x)[q] = kPending;
+  }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     header[kTicketL] = 0;
     header[kTicketU] = 0;
@@ -146,11 +149,12 @@ __global__ void __launch_bounds__(kTriWarps * 32) tri_solve_kernel(
     int32_t n, int32_t chunk, int32_t nchunks, const int32_t* __restrict__ bnd, const int32_t* __restrict__ rp,
     const int32_t* __restrict__ ci, const TV* __restrict__ vals, const TV* __restrict__ dinv,
     const int32_t* __restrict__ ord, const int32_t* __restrict__ tick, const double* rhs, double* out,
-    double* pend_out, int32_t* header, long long spin_ns, int32_t skip_row, int32_t* stop) {
+    int32_t* header, long long spin_ns, int32_t skip_row, int32_t* stop) {
   constexpr int G = groups_for(B);
+  using VB = ValueBits<TV>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  double* yl = reinterpret_cast<double*>(smem_raw);
-  int* s_i = reinterpret_cast<int*>(yl + (size_t)chunk * B);
+  TV* yl = reinterpret_cast<TV*>(smem_raw);  // the chunk's values, in the type they are used in
+  int* s_i = reinterpret_cast<int*>(smem_raw + (((size_t)chunk * B * sizeof(TV) + 15) & ~(size_t)15));
   int* s_beg = s_i + chunk;
   int* s_end = s_beg + chunk;
   __shared__ int s_c;
@@ -180,7 +184,7 @@ __global__ void __launch_bounds__(kTriWarps * 32) tri_solve_kernel(
       s_beg[q] = rp[i];
       s_end[q] = rp[i + 1];
     }
-    for (int q = tid; q < len * B; q += blockDim.x) reinterpret_cast<unsigned long long*>(yl)[q] = kPending;
+    for (int q = tid; q < len * B; q += blockDim.x) reinterpret_cast<typename VB::U*>(yl)[q] = VB::kPend;
     __syncthreads();
     RowPre<B, UPPER, TV> cur, nx1, nx2;
     fetch_row<B, UPPER, TV>(cur, warp, len, s_i, s_beg, s_end, ci, vals, dinv, rhs, g, rr, act, lane);
@@ -226,10 +230,11 @@ __global__ void __launch_bounds__(kTriWarps * 32) tri_solve_kernel(
               yv[q] = kPending;
             }
           }
-          double yj[B];
+          TV yt[B];
           if (j >= lo && j < hi) {
-            ok = wait_values_shared<B>(yl + (size_t)(j - lo) * B, yj, w);
+            ok = wait_values_shared<B, TV>(yl + (size_t)(j - lo) * B, yt, w);
           } else {
+            double yj[B];
             bool have = true;
 #pragma unroll
             for (int q = 0; q < B; ++q) {
@@ -237,10 +242,12 @@ __global__ void __launch_bounds__(kTriWarps * 32) tri_solve_kernel(
               yj[q] = __longlong_as_double((long long)yv[q]);
             }
             if (!have) ok = wait_values<B>(out + (size_t)j * B, yj, w);
+#pragma unroll
+            for (int q = 0; q < B; ++q) yt[q] = (TV)yj[q];
           }
           if (ok) {
 #pragma unroll
-            for (int q = 0; q < B; ++q) acc = fma(av[q], (TV)yj[q], acc);
+            for (int q = 0; q < B; ++q) acc = fma(av[q], yt[q], acc);
           }
         }
       }
@@ -250,14 +257,13 @@ __global__ void __launch_bounds__(kTriWarps * 32) tri_solve_kernel(
       }
 #pragma unroll
       for (int d = G / 2; d >= 1; d >>= 1) acc += __shfl_down_sync(kFull, acc, d * B);
-      double v = 0.0;
       if (lane < B) {
-        v = (double)(own - acc);
-        unsigned long long u = (unsigned long long)__double_as_longlong(v);
-        if (u == kPending) u = kQuietNaN;
-        reinterpret_cast<volatile unsigned long long*>(yl)[(size_t)(i - lo) * B + lane] = u;
-        if (i != skip_row) publish(out + (size_t)i * B + lane, v);
-        if (!UPPER) reinterpret_cast<unsigned long long*>(pend_out)[(size_t)i * B + lane] = kPending;
+        // the chunk's own readers first (shared memory, type TV), then global
+        const TV vt = own - acc;
+        typename VB::U u = VB::bits(vt);
+        if (u == VB::kPend) u = VB::kQuiet;
+        reinterpret_cast<volatile typename VB::U*>(yl)[(size_t)(i - lo) * B + lane] = u;
+        if (i != skip_row) publish(out + (size_t)i * B + lane, (double)vt);
       }
       cur = nx1;
       nx1 = nx2;
@@ -276,7 +282,10 @@ int sm_count() {
   return cached;
 }
 
-size_t tri_smem_bytes(int chunk, int b) { return (size_t)chunk * (b * sizeof(double) + 3 * sizeof(int)); }
+template <typename TV>
+size_t tri_smem_bytes(int chunk, int b) {
+  return align_up16((size_t)chunk * b * sizeof(TV)) + (size_t)chunk * 3 * sizeof(int);
+}
 
 // Persistent grid: as many CTAs as fit on the device at once (cached per
 // shared-memory size; the occupancy query is host work worth skipping per
@@ -303,19 +312,19 @@ void launch_solves(const bilu_pattern* p, int chunk, int nchunks, const TV* L, c
                    int32_t* stop, void* stream) {
   cudaStream_t s = (cudaStream_t)stream;
   const int32_t n = p->n;
-  const size_t smem = tri_smem_bytes(chunk, B);
+  const size_t smem = tri_smem_bytes<TV>(chunk, B);
   {
     const int grid = tri_grid<B, false, TV, W>(smem, nchunks);
     ProfScope ps(BILU_PROF_LOWER, stream);
     tri_solve_kernel<B, false, TV, W><<<grid, W * 32, smem, s>>>(n, chunk, nchunks, p->solve.d_bnd, p->d_lrp, p->d_lci, L,
-                                                                 nullptr, p->solve.d_ord_l, p->solve.d_tick_l, r, y, x,
+                                                                 nullptr, p->solve.d_ord_l, p->solve.d_tick_l, r, y,
                                                                  header, cfg.spin_ns, cfg.skip_row, stop);
   }
   {
     const int grid = tri_grid<B, true, TV, W>(smem, nchunks);
     ProfScope ps(BILU_PROF_UPPER, stream);
     tri_solve_kernel<B, true, TV, W><<<grid, W * 32, smem, s>>>(n, chunk, nchunks, p->solve.d_bnd, p->d_urp, p->d_uci, U, Dinv,
-                                                                p->solve.d_ord_u, p->solve.d_tick_u, y, x, nullptr, header,
+                                                                p->solve.d_ord_u, p->solve.d_tick_u, y, x, header,
                                                                 cfg.spin_ns, -1, stop);
   }
 }
@@ -340,7 +349,7 @@ int launch_apply_t(const bilu_pattern* p, int32_t b, const TV* f, const double* 
   const int prep_blocks = (int)std::min<long long>((m + 255) / 256, (long long)sm_count() * 8);
   {
     ProfScope ps(BILU_PROF_APPLY_PREP, stream);
-    apply_prep_kernel<<<prep_blocks, 256, 0, s>>>(y, m, header, stop);
+    apply_prep_kernel<<<prep_blocks, 256, 0, s>>>(y, x, m, header, stop);
   }
   BILU_DISPATCH_B(b, {
     if (cfg.warps == 16)
