@@ -47,11 +47,11 @@ FP64_PEAK_TFLOPS = 1.196  # measured FP64 FMA rate of this GB300 (FMA = 2 flops)
 # the summary and the command); keyed by (workload, k, kernel).  The capture
 # ran on the 96 x 96 x 48 case (the recipe's size rule); a solve streams each
 # factor block once, so its traffic is scaled to the 128 x 128 x 64 launch by
-# the algorithmic bytes (measured traffic / algorithmic = 1.041 for the upper
-# solve, 1.081 for the lower, 0.990 for the SpMV).  Missing entries report null.
+# the algorithmic bytes (measured traffic / algorithmic = 1.044 for the upper
+# solve, 1.048 for the lower, 0.989 for the SpMV).  Missing entries report null.
 NCU_TRAFFIC = {
-    ("grid128x128x64_7pt_b3", 1, "upper_solve"): 625379682,
-    ("grid128x128x64_7pt_b3", 1, "lower_solve"): 567597803,
+    ("grid128x128x64_7pt_b3", 1, "upper_solve"): 626915781,
+    ("grid128x128x64_7pt_b3", 1, "lower_solve"): 550252912,
 }
 
 
