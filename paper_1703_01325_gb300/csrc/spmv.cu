@@ -26,12 +26,15 @@ template <typename TV>
 __device__ __forceinline__ TV ld_stream(const TV* p) { return __ldcs(p); }
 
 // TV: the type the matrix is stored in and the products are accumulated in
-// (double, or float for the mixed-precision solver); x and y stay double.
-template <int B, typename TV>
+// (double, or float for the mixed-precision solver); y stays double.  XT: the
+// type of x -- double, or (inside the mixed-precision solver) an FP32 copy of
+// x made once per product, since a double -> float conversion per use runs at
+// the FP64 rate and would bound the FP32 kernel like the FP64 one.
+template <int B, typename TV, typename XT>
 __global__ void __launch_bounds__(256) spmv_kernel(int32_t n, const int32_t* __restrict__ rp,
                                                    const int32_t* __restrict__ ci,
                                                    const TV* __restrict__ vals,
-                                                   const double* __restrict__ x,
+                                                   const XT* __restrict__ x,
                                                    double* __restrict__ y,
                                                    const int32_t* stop) {
   constexpr int R = 32 / B;
@@ -52,7 +55,7 @@ __global__ void __launch_bounds__(256) spmv_kernel(int32_t n, const int32_t* __r
 #pragma unroll
       for (int u = 0; u < U; ++u) j[u] = __ldg(ci + t + u);
       TV av[U][B];
-      double xv[U][B];
+      XT xv[U][B];
 #pragma unroll
       for (int u = 0; u < U; ++u) {
         const TV* a = vals + (size_t)(t + u) * (B * B) + r;
@@ -72,7 +75,7 @@ __global__ void __launch_bounds__(256) spmv_kernel(int32_t n, const int32_t* __r
   for (; t < end; ++t) {
     const int32_t j = __ldg(ci + t);
     const TV* a = vals + (size_t)t * (B * B) + r;
-    const double* xj = x + (size_t)j * B;
+    const XT* xj = x + (size_t)j * B;
     TV av[B];
 #pragma unroll
     for (int c = 0; c < B; ++c) av[c] = ld_stream(a + c * B);
@@ -82,14 +85,16 @@ __global__ void __launch_bounds__(256) spmv_kernel(int32_t n, const int32_t* __r
   y[row * B + r] = (double)acc;
 }
 
-__global__ void convert_kernel(const double* __restrict__ src, float* __restrict__ dst, long long count) {
+__global__ void convert_kernel(const double* __restrict__ src, float* __restrict__ dst, long long count,
+                               const int32_t* stop) {
+  if (stop && ld_volatile_s32(stop)) return;
   const long long stride = (long long)gridDim.x * blockDim.x;
   for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < count; q += stride)
     dst[q] = (float)src[q];
 }
 
-template <typename TV>
-int launch_spmv_t(int32_t n, int32_t b, const int32_t* rp, const int32_t* ci, const TV* vals, const double* x,
+template <typename TV, typename XT>
+int launch_spmv_t(int32_t n, int32_t b, const int32_t* rp, const int32_t* ci, const TV* vals, const XT* x,
                   double* y, void* stream, const int32_t* stop) {
   if (n == 0) return 0;
   cudaStream_t s = (cudaStream_t)stream;
@@ -99,7 +104,7 @@ int launch_spmv_t(int32_t n, int32_t b, const int32_t* rp, const int32_t* ci, co
     const int tpb = 256;
     const long long blocks = (warps * 32 + tpb - 1) / tpb;
     ProfScope ps(BILU_PROF_SPMV, stream);
-    spmv_kernel<B, TV><<<(unsigned)blocks, tpb, 0, s>>>(n, rp, ci, vals, x, y, stop);
+    spmv_kernel<B, TV, XT><<<(unsigned)blocks, tpb, 0, s>>>(n, rp, ci, vals, x, y, stop);
   });
   return (int)cudaGetLastError();
 }
@@ -108,21 +113,26 @@ int launch_spmv_t(int32_t n, int32_t b, const int32_t* rp, const int32_t* ci, co
 
 int launch_spmv(int32_t n, int32_t b, const int32_t* rp, const int32_t* ci, const double* vals,
                 const double* x, double* y, void* stream, const int32_t* stop) {
-  return launch_spmv_t<double>(n, b, rp, ci, vals, x, y, stream, stop);
+  return launch_spmv_t<double, double>(n, b, rp, ci, vals, x, y, stream, stop);
 }
 
 int launch_spmv_f32(int32_t n, int32_t b, const int32_t* rp, const int32_t* ci, const float* vals,
                     const double* x, double* y, void* stream, const int32_t* stop) {
-  return launch_spmv_t<float>(n, b, rp, ci, vals, x, y, stream, stop);
+  return launch_spmv_t<float, double>(n, b, rp, ci, vals, x, y, stream, stop);
 }
 
-int launch_convert_f32(const double* src, float* dst, long long count, void* stream) {
+int launch_spmv_f32x(int32_t n, int32_t b, const int32_t* rp, const int32_t* ci, const float* vals,
+                     const float* x32, double* y, void* stream, const int32_t* stop) {
+  return launch_spmv_t<float, float>(n, b, rp, ci, vals, x32, y, stream, stop);
+}
+
+int launch_convert_f32(const double* src, float* dst, long long count, void* stream, const int32_t* stop) {
   if (count <= 0) return 0;
   int dev = 0, sms = 1;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const long long blocks = std::min<long long>((count + 255) / 256, (long long)sms * 16);
-  convert_kernel<<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(src, dst, count);
+  convert_kernel<<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(src, dst, count, stop);
   return (int)cudaGetLastError();
 }
 
