@@ -15,16 +15,19 @@
 extern "C" {
 #endif
 
-/* Consecutive block rows one CTA owns in the sync-free triangular solves
- * (default 256).  Dependencies inside a chunk resolve through shared memory,
- * dependencies across chunks through global memory.  1 <= rows <= 1024, else
- * BILU_ERR_ARG.  The per-chunk row order is rebuilt (host work plus one
+/* Target of consecutive block rows one CTA owns in the sync-free triangular
+ * solves.  Dependencies inside a chunk resolve through shared memory,
+ * dependencies across chunks through global memory.  0 (the default) picks
+ * per pattern: n / (10 * SMs) rows, clamped to [32, 256], so that small
+ * systems still spread over the GPU; 1 <= rows <= 1024 fixes the target;
+ * other values: BILU_ERR_ARG.  The schedule is rebuilt (host work plus one
  * device allocation) by the next apply or solve on each pattern. */
 int bilu_set_trisolve_chunk(int32_t rows);
 int32_t bilu_get_trisolve_chunk(void);
 
-/* Consecutive block rows one CTA owns in the sync-free factorization
- * (default 512), 1 <= rows <= 1024, else BILU_ERR_ARG.  Its schedule is
+/* Target of consecutive block rows one CTA owns in the sync-free
+ * factorization: 0 (the default) picks n / (2 * SMs) clamped to [64, 512];
+ * 1 <= rows <= 1024 fixes it; other values: BILU_ERR_ARG.  Its schedule is
  * separate from the solves' and is rebuilt by the next factorization. */
 int bilu_set_factor_chunk(int32_t rows);
 int32_t bilu_get_factor_chunk(void);

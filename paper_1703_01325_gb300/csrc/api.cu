@@ -16,12 +16,12 @@ namespace {
 bool valid_b(int32_t b) { return b >= 1 && b <= 8; }
 
 // The schedules the factorization and the solves run on, rebuilt (host work
-// plus one device allocation) when the configured chunk size changed.
+// plus one device allocation) when the chunk target changed.
 int solve_schedule(const bilu_pattern* p) {
-  return ensure_schedule(p, &const_cast<bilu_pattern*>(p)->solve, trisolve_config().chunk, true);
+  return ensure_schedule(p, &const_cast<bilu_pattern*>(p)->solve, solve_chunk_target(p->n), true);
 }
 int factor_schedule(const bilu_pattern* p) {
-  return ensure_schedule(p, &const_cast<bilu_pattern*>(p)->fact, trisolve_config().factor_chunk, false);
+  return ensure_schedule(p, &const_cast<bilu_pattern*>(p)->fact, factor_chunk_target(p->n), false);
 }
 
 int ready(const bilu_pattern* p) {
@@ -101,8 +101,8 @@ extern "C" int bilu_pattern_upload(bilu_pattern* p, void* stream) {
   }
   p->d_mem = mem;
   p->device = dev;
-  if (ensure_schedule(p, &p->solve, trisolve_config().chunk, true) != 0 ||
-      (!p->is_transpose && ensure_schedule(p, &p->fact, trisolve_config().factor_chunk, false) != 0))
+  if (ensure_schedule(p, &p->solve, solve_chunk_target(p->n), true) != 0 ||
+      (!p->is_transpose && ensure_schedule(p, &p->fact, factor_chunk_target(p->n), false) != 0))
     return BILU_ERR_OOM;
   return BILU_OK;
 }
@@ -381,7 +381,7 @@ extern "C" int bicgstab_solve_mixed(const bilu_pattern* p, const bilu_bsr* A, co
 // ---- tuning and test hooks (include/bilu_tuning.h) ----
 
 extern "C" int bilu_set_trisolve_chunk(int32_t rows) {
-  if (rows < 1 || rows > 1024) return BILU_ERR_ARG;
+  if (rows < 0 || rows > 1024) return BILU_ERR_ARG;
   trisolve_config().chunk = rows;
   return BILU_OK;
 }
@@ -389,7 +389,7 @@ extern "C" int bilu_set_trisolve_chunk(int32_t rows) {
 extern "C" int32_t bilu_get_trisolve_chunk(void) { return trisolve_config().chunk; }
 
 extern "C" int bilu_set_factor_chunk(int32_t rows) {
-  if (rows < 1 || rows > 1024) return BILU_ERR_ARG;
+  if (rows < 0 || rows > 1024) return BILU_ERR_ARG;
   trisolve_config().factor_chunk = rows;
   return BILU_OK;
 }

@@ -87,13 +87,18 @@ constexpr long long kDefaultSpinNs = 2000000000LL;  // 2 s
 
 // Tunables of the sync-free triangular solves (see trisolve.cu).
 struct TrisolveConfig {
-  int chunk = 256;         // consecutive block rows one CTA of the solves owns
+  int chunk = 0;           // target rows per CTA of the solves (0: by size)
   int warps = 4;           // warps per CTA of the solves (4, 8 or 16)
-  int factor_chunk = 512;  // consecutive block rows one CTA of the factorization owns
+  int factor_chunk = 0;    // target rows per CTA of the factorization (0: by size)
   long long spin_ns = kDefaultSpinNs;
   int skip_row = -1;       // test hook: this row of the lower solve is never published
 };
 TrisolveConfig& trisolve_config();
+// The chunk targets in effect for a system of n block rows: the configured
+// ones, or (0) n / (10 * SMs) in [32, 256] for the solves and n / (2 * SMs) in
+// [64, 512] for the factorization -- enough chunks to fill the GPU.
+int32_t solve_chunk_target(int32_t n);
+int32_t factor_chunk_target(int32_t n);
 
 // Brackets one kernel launch with profiling events (when enabled) and counts it.
 class ProfScope {

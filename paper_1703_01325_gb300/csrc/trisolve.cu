@@ -50,6 +50,32 @@ TrisolveConfig& trisolve_config() {
 }
 
 namespace {
+int device_sm_count() {
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) !=
+                                                 cudaSuccess || sms <= 0) {
+    cudaGetLastError();
+    return 1;
+  }
+  return sms;
+}
+}  // namespace
+
+int32_t solve_chunk_target(int32_t n) {
+  const int c = trisolve_config().chunk;
+  if (c > 0) return c;
+  const long long t = (long long)n / (10LL * device_sm_count());
+  return (int32_t)std::max(32LL, std::min(256LL, t));
+}
+
+int32_t factor_chunk_target(int32_t n) {
+  const int c = trisolve_config().factor_chunk;
+  if (c > 0) return c;
+  const long long t = (long long)n / (2LL * device_sm_count());
+  return (int32_t)std::max(64LL, std::min(512LL, t));
+}
+
+namespace {
 
 
 __global__ void apply_prep_kernel(double* y, double* x, long long m, int32_t* header, const int32_t* stop) {
