@@ -329,3 +329,27 @@ def test_full_size_gmres_fixed_steps(B, full_size):
         res = np.linalg.norm(S.rhs - o.spmv(xg)) / np.linalg.norm(S.rhs)
         assert res == pytest.approx(sinfo.true_relres, rel=1e-6)
         assert rro == pytest.approx(sinfo.true_relres, rel=1e-6)
+
+
+@pytest.mark.parametrize("fp32", [False, True])
+def test_apply_input_holding_the_pending_pattern(B, fp32):
+    """A right-hand side entry that carries the solves' internal "pending" bit
+    pattern (a signalling NaN) must not stall them: every computed value is
+    stored as a quiet NaN instead, the apply completes with status 0 and the
+    rows it reaches are NaN while the others match the clean apply."""
+    S = reservoir_system(9, 7, 5, 3, sigma=1.0, accum=0.01, seed=3)
+    rp, ci, vals, rhs = device_system(S, DEV)
+    P = B.bilu_symbolic(S.n, S.row_ptr, S.col_idx, 1).upload()
+    F, _ = B.bilu_factor(P, 3, vals)
+    Fa = B.bilu_convert_f32(F) if fp32 else F
+    apply = B.bilu_apply_f32 if fp32 else B.bilu_apply
+    bad = rhs.clone()
+    bits = bad.view(torch.int64)
+    bits[7 * 3 + 1] = 0x7FF4DEADBEEF0001
+    work = B.workspace(P.apply_workspace_bytes(3))
+    x = apply(P, 3, Fa, bad, work=work).cpu().numpy()
+    assert B.bilu_workspace_status(work) == 0
+    clean = apply(P, 3, Fa, rhs).cpu().numpy()
+    nan = np.isnan(x)
+    assert nan.any() and not np.isnan(clean).any()
+    assert np.array_equal(x[~nan], clean[~nan])
