@@ -309,7 +309,9 @@ def precision_compare(B, dev, stream, cases=((2, 1), (4, 1)), tol=1e-8):
     inside FP64 iterative refinement (bilu_factor_f32 + bicgstab_solve_mixed);
     "f32prec" = FP64 BiCGSTAB with the FP32-stored preconditioner
     (bilu_factor_f32 + bicgstab_solve_f32prec); "f32prec_from_fp64" = the same
-    with the FP64 factors rounded to FP32 (bilu_factor + bilu_convert_f32).
+    with the FP64 factors rounded to FP32 (bilu_factor + bilu_convert_f32);
+    "fp64_gmres20" = the FP64 preconditioner in restarted GMRES(20), the
+    solver of the paper's experiments (bilu_factor + gmres_solve).
     Times include the factorization.  Each solution's distance to the FP64 one (which the parity
     tests hold to the CPU oracle) is reported as its error."""
     import torch
@@ -352,10 +354,16 @@ def precision_compare(B, dev, stream, cases=((2, 1), (4, 1)), tol=1e-8):
             xq.zero_()
             return B.bicgstab_solve_f32prec(P, A, F32, rhs, x=xq, tol=tol, maxit=5000, work=sw)[1]
 
-        xp, xq = torch.zeros_like(rhs), torch.zeros_like(rhs)
+        def gmres20():
+            B.bilu_factor(P, b, vals, F, fw)
+            xg.zero_()
+            return B.gmres_solve(P, A, F, rhs, x=xg, tol=tol, maxit=5000, restart=20, work=gw)[1]
+
+        xp, xq, xg = torch.zeros_like(rhs), torch.zeros_like(rhs), torch.zeros_like(rhs)
+        gw = B.workspace(int(B.L.load().gmres_workspace_bytes(P.handle, b, 20)), dev)
         row = {"workload": "grid96x96x48_7pt", "b": b, "k": k}
         for name, fn in (("fp64", fp64), ("mixed", mixed), ("f32prec", f32prec),
-                         ("f32prec_from_fp64", f32prec_from_fp64)):
+                         ("f32prec_from_fp64", f32prec_from_fp64), ("fp64_gmres20", gmres20)):
             fn()  # warm-up
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             torch.cuda.synchronize()
