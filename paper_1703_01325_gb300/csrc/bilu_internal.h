@@ -119,9 +119,6 @@ int launch_spmv(int32_t n, int32_t b, const int32_t* rp, const int32_t* ci, cons
                 const double* x, double* y, void* stream, const int32_t* stop = nullptr);
 int launch_spmv_f32(int32_t n, int32_t b, const int32_t* rp, const int32_t* ci, const float* vals,
                     const double* x, double* y, void* stream, const int32_t* stop = nullptr);
-// y = A x with FP32 values and an FP32 copy of x (the mixed solver's inner SpMV)
-int launch_spmv_f32x(int32_t n, int32_t b, const int32_t* rp, const int32_t* ci, const float* vals,
-                     const float* x32, double* y, void* stream, const int32_t* stop = nullptr);
 int launch_convert_f32(const double* src, float* dst, long long count, void* stream,
                        const int32_t* stop = nullptr);
 

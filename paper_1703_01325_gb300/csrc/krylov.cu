@@ -302,8 +302,7 @@ size_t krylov_workspace_bytes(int32_t n, int32_t b) {
 
 size_t krylov_mixed_workspace_bytes(int32_t n, int32_t b) {
   const size_t vec = align256((size_t)n * b * sizeof(double));
-  const size_t vec32 = align256((size_t)n * b * sizeof(float));
-  return krylov_workspace_bytes(n, b) + 2 * vec + 256 + vec32;
+  return krylov_workspace_bytes(n, b) + 2 * vec + 256;
 }
 
 // BiCGSTAB on the operators of `ops`; `x` holds the start vector.  With
@@ -477,12 +476,10 @@ int run_bicgstab_mixed(const bilu_pattern* p, const bilu_bsr* A, const float* va
   double* rout = reinterpret_cast<double*>(tail);
   double* d = reinterpret_cast<double*>(tail + vec);
   double* norms = reinterpret_cast<double*>(tail + 2 * vec);  // [(r, r), (rhs, rhs)]
-  float* x32 = reinterpret_cast<float*>(tail + 2 * vec + 256);  // FP32 copy of the SpMV's input
   double* partials = reinterpret_cast<double*>(reinterpret_cast<char*>(work) + align256(sizeof(KState)));
   KOps ops;
   ops.spmv = [=](const double* xin, double* yout, int32_t* stop, void*) {
-    const int e = launch_convert_f32(xin, x32, m, stream, stop);
-    return e ? e : launch_spmv_f32x(n, b, A->row_ptr, A->col_idx, vals32, x32, yout, stream, stop);
+    return launch_spmv_f32(n, b, A->row_ptr, A->col_idx, vals32, xin, yout, stream, stop);
   };
   ops.apply = [=](const double* rin, double* zout, int32_t* stop, void* aw) {
     return launch_apply_f32(p, b, f32, rin, zout, aw, stop, stream);

@@ -11,7 +11,8 @@
 // In FP64 the kernel is bound by the FP64 pipe; in FP32 it is bound by load
 // latency, so the FP32 kernel issues the loads of four blocks (column
 // indices, then values and x) before their FMAs, which run in the same order
-// as one block at a time (identical sums).
+// as one block at a time (identical sums).  The FP32 kernel takes x in FP64
+// and rounds it to nearest on the integer pipes, one component per lane.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -25,11 +26,16 @@ namespace {
 template <typename TV>
 __device__ __forceinline__ TV ld_stream(const TV* p) { return __ldcs(p); }
 
+// FP32 values with FP64 x: each lane of a row converts one component of x_j
+// (on the integer pipes, d2f_rn) and the row's b lanes share the components
+// by shuffles, instead of every lane converting all b.
+template <typename TV, typename XT>
+constexpr bool kShareX = sizeof(TV) == 4 && sizeof(XT) == 8;
+
 // TV: the type the matrix is stored in and the products are accumulated in
-// (double, or float for the mixed-precision solver); y stays double.  XT: the
-// type of x -- double, or (inside the mixed-precision solver) an FP32 copy of
-// x made once per product, since a double -> float conversion per use runs at
-// the FP64 rate and would bound the FP32 kernel like the FP64 one.
+// (double, or float for the FP32 copy of A); y stays double.  XT: the type of
+// x (double).  A hardware double -> float conversion runs at the FP64 rate and
+// would bound the FP32 kernel like the FP64 one, hence d2f_rn and the sharing.
 template <int B, typename TV, typename XT>
 __global__ void __launch_bounds__(256) spmv_kernel(int32_t n, const int32_t* __restrict__ rp,
                                                    const int32_t* __restrict__ ci,
@@ -47,6 +53,9 @@ __global__ void __launch_bounds__(256) spmv_kernel(int32_t n, const int32_t* __r
   if (q >= R || row >= n) return;
   const int32_t beg = rp[row], end = rp[row + 1];
   TV acc = TV(0);
+  // The b lanes of this row: they run the same trip counts, so they meet at every shuffle.
+  const unsigned am = (B == 32 ? 0xFFFFFFFFu : ((1u << B) - 1u)) << (q * B);
+  (void)am;
   constexpr int U = sizeof(TV) == 4 ? 4 : 1;  // blocks whose loads are in flight together
   int32_t t = beg;
   if (U > 1) {
@@ -62,14 +71,24 @@ __global__ void __launch_bounds__(256) spmv_kernel(int32_t n, const int32_t* __r
 #pragma unroll
         for (int c = 0; c < B; ++c) av[u][c] = ld_stream(a + c * B);
       }
+      if constexpr (kShareX<TV, XT>) {
+        TV xs[U];
 #pragma unroll
-      for (int u = 0; u < U; ++u)
+        for (int u = 0; u < U; ++u) xs[u] = d2f_rn(__ldg(x + (size_t)j[u] * B + r));
 #pragma unroll
-        for (int c = 0; c < B; ++c) xv[u][c] = __ldg(x + (size_t)j[u] * B + c);
+        for (int u = 0; u < U; ++u)
 #pragma unroll
-      for (int u = 0; u < U; ++u)
+          for (int c = 0; c < B; ++c) acc = fma(av[u][c], __shfl_sync(am, xs[u], lane - r + c), acc);
+      } else {
 #pragma unroll
-        for (int c = 0; c < B; ++c) acc = fma(av[u][c], (TV)xv[u][c], acc);
+        for (int u = 0; u < U; ++u)
+#pragma unroll
+          for (int c = 0; c < B; ++c) xv[u][c] = __ldg(x + (size_t)j[u] * B + c);
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+#pragma unroll
+          for (int c = 0; c < B; ++c) acc = fma(av[u][c], (TV)xv[u][c], acc);
+      }
     }
   }
   for (; t < end; ++t) {
@@ -79,8 +98,14 @@ __global__ void __launch_bounds__(256) spmv_kernel(int32_t n, const int32_t* __r
     TV av[B];
 #pragma unroll
     for (int c = 0; c < B; ++c) av[c] = ld_stream(a + c * B);
+    if constexpr (kShareX<TV, XT>) {
+      const TV xs = d2f_rn(__ldg(xj + r));
 #pragma unroll
-    for (int c = 0; c < B; ++c) acc = fma(av[c], (TV)__ldg(xj + c), acc);
+      for (int c = 0; c < B; ++c) acc = fma(av[c], __shfl_sync(am, xs, lane - r + c), acc);
+    } else {
+#pragma unroll
+      for (int c = 0; c < B; ++c) acc = fma(av[c], (TV)__ldg(xj + c), acc);
+    }
   }
   y[row * B + r] = (double)acc;
 }
@@ -90,7 +115,7 @@ __global__ void convert_kernel(const double* __restrict__ src, float* __restrict
   if (stop && ld_volatile_s32(stop)) return;
   const long long stride = (long long)gridDim.x * blockDim.x;
   for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < count; q += stride)
-    dst[q] = (float)src[q];
+    dst[q] = d2f_rn(src[q]);
 }
 
 template <typename TV, typename XT>
@@ -119,11 +144,6 @@ int launch_spmv(int32_t n, int32_t b, const int32_t* rp, const int32_t* ci, cons
 int launch_spmv_f32(int32_t n, int32_t b, const int32_t* rp, const int32_t* ci, const float* vals,
                     const double* x, double* y, void* stream, const int32_t* stop) {
   return launch_spmv_t<float, double>(n, b, rp, ci, vals, x, y, stream, stop);
-}
-
-int launch_spmv_f32x(int32_t n, int32_t b, const int32_t* rp, const int32_t* ci, const float* vals,
-                     const float* x32, double* y, void* stream, const int32_t* stop) {
-  return launch_spmv_t<float, float>(n, b, rp, ci, vals, x32, y, stream, stop);
 }
 
 int launch_convert_f32(const double* src, float* dst, long long count, void* stream, const int32_t* stop) {

@@ -165,3 +165,21 @@ def test_bicgstab_f32prec_reaches_fp64_accuracy(B, k):
     xo, _, _, st = oracle.bicgstab(S.n, 3, S.row_ptr, S.col_idx, S.vals, o.prp, o.pci, o.F, o.Dinv, S.rhs,
                                    tol=1e-12, maxit=2000)
     assert st == 0 and np.linalg.norm(xg - xo) <= 1e-7 * np.linalg.norm(xo)
+
+
+def test_convert_f32_bit_exact_on_many_values(B):
+    """bilu_convert_f32 (integer-pipe rounding with a hardware fallback at the
+    edges) agrees bit for bit with round-to-nearest-even: a million values over
+    80 decades, values exactly halfway between floats, and the edge cases."""
+    rng = np.random.default_rng(7)
+    parts = [rng.standard_normal(1_000_000) * 10.0 ** rng.integers(-40, 40, 1_000_000)]
+    f = rng.standard_normal(100_000).astype(np.float32)
+    half_ulp = np.spacing(f).astype(np.float64) / 2
+    parts += [f.astype(np.float64) + half_ulp, f.astype(np.float64) - half_ulp]
+    parts.append(np.array([0.0, -0.0, 1e-40, -1e-45, 3.4028234663852886e38, 3.4028235677973366e38, 3.5e38,
+                           -1e300, np.inf, -np.inf, 1.1754943508222875e-38, 1.1754942e-38]))
+    x = np.concatenate(parts)
+    got = B.bilu_convert_f32(torch.from_numpy(x).to(DEV)).cpu().numpy()
+    with np.errstate(over="ignore"):
+        ref = x.astype(np.float32)
+    assert np.array_equal(got.view(np.uint32), ref.view(np.uint32))
