@@ -222,16 +222,18 @@ __global__ void __launch_bounds__(kTriWarps * 32) tri_solve_kernel(
                               act, lane);
       fetch_deps<B, UPPER, TV>(nx1, out, lo, hi, lane);
       const int i = cur.i;
-      TV acc = TV(0);
       bool ok = true;
-      // the row's own term in TV, formed before the waits (FP32 U': D_i^{-1} y_i here)
-      TV own = TV(0);
+      // The row's own term in TV, formed before the waits (FP32 U': D_i^{-1} y_i
+      // here), seeds the sum of group 0 (lanes < B); the blocks then accumulate
+      // as fma(-a, y, acc), so the reduced sum is the row's value with no final
+      // subtraction (one FP64 instruction and its latency fewer per row).
+      TV acc = TV(0);
       if (lane < B) {
         if (UPPER && !kFoldOwn<TV>) {
 #pragma unroll
-          for (int q = 0; q < B; ++q) own = fma(cur.d[q], (TV)cur.yi[q], own);
+          for (int q = 0; q < B; ++q) acc = fma(cur.d[q], (TV)cur.yi[q], acc);
         } else {
-          own = (TV)cur.own;
+          acc = (TV)cur.own;
         }
       }
       for (int t0 = cur.beg; t0 < cur.end; t0 += G) {
@@ -273,7 +275,7 @@ __global__ void __launch_bounds__(kTriWarps * 32) tri_solve_kernel(
           }
           if (ok) {
 #pragma unroll
-            for (int q = 0; q < B; ++q) acc = fma(av[q], yt[q], acc);
+            for (int q = 0; q < B; ++q) acc = fma(-av[q], yt[q], acc);
           }
         }
       }
@@ -285,7 +287,7 @@ __global__ void __launch_bounds__(kTriWarps * 32) tri_solve_kernel(
       for (int d = G / 2; d >= 1; d >>= 1) acc += __shfl_down_sync(kFull, acc, d * B);
       if (lane < B) {
         // the chunk's own readers first (shared memory, type TV), then global
-        const TV vt = own - acc;
+        const TV vt = acc;
         typename VB::U u = VB::bits(vt);
         if (u == VB::kPend) u = VB::kQuiet;
         reinterpret_cast<volatile typename VB::U*>(yl)[(size_t)(i - lo) * B + lane] = u;

@@ -220,7 +220,16 @@ def test_bicgstab_small_workload(B, k):
                                         S.rhs, tol=1e-8, maxit=1000)
     assert info.status == 0 and sto == 0
     assert info.true_relres <= 1e-8 and rro <= 1e-8
-    assert abs(info.iters - ito) <= 2
+    # BiCGSTAB's iteration count is not a continuous function of rounding: the
+    # oracle's own count moves by several iterations (57..61 at k = 0) when the
+    # rhs is perturbed at 1e-15 relative.  The GPU count, whose sums round in a
+    # different order, must lie within that spread, widened by 2.
+    its = [ito]
+    for seed in range(1, 7):
+        pert = S.rhs * (1.0 + 1e-15 * np.random.default_rng(seed).standard_normal(S.rhs.shape))
+        its.append(oracle.bicgstab(S.n, 3, S.row_ptr, S.col_idx, S.vals, o.prp, o.pci, o.F, o.Dinv,
+                                   pert, tol=1e-8, maxit=1000)[1])
+    assert min(its) - 2 <= info.iters <= max(its) + 2, (info.iters, its)
     # the reported residual is the true one: recompute it with the oracle's SpMV
     xg = x.cpu().numpy()
     res = np.linalg.norm(S.rhs - oracle.spmv(S.n, 3, S.row_ptr, S.col_idx, S.vals, xg)) / np.linalg.norm(S.rhs)
