@@ -42,6 +42,7 @@ struct bilu_pattern {
   int32_t nlev_l = 0, nlev_u = 0;
   // Strictly lower / strictly upper parts of P' as separate CSR structures.
   std::vector<int32_t> lrp, lci, urp, uci;
+  int32_t max_l = 0, max_u = 0;  // most blocks in a row of L / of U'
   // Backfill gather map: for every factor slot in [L | D | U] the A block that
   // lands there, or -1 for a fill block (Algorithm 5 steps 3-4).  For a
   // transposed pattern (is_transpose): the slot of the source pattern's factor

@@ -72,6 +72,7 @@ void finish_pattern(bilu_pattern* p) {
   p->nlev_u = mu + 1;
 
   // Split P' into strictly lower and strictly upper CSR structures.
+  p->max_l = p->max_u = 0;
   p->lrp.assign((size_t)n + 1, 0);
   p->urp.assign((size_t)n + 1, 0);
   for (int32_t i = 0; i < n; ++i) {
@@ -82,6 +83,8 @@ void finish_pattern(bilu_pattern* p) {
     }
     p->lrp[(size_t)i + 1] = p->lrp[i] + nl;
     p->urp[(size_t)i + 1] = p->urp[i] + nu;
+    p->max_l = std::max(p->max_l, nl);
+    p->max_u = std::max(p->max_u, nu);
   }
   p->lci.resize((size_t)p->lrp[n]);
   p->uci.resize((size_t)p->urp[n]);

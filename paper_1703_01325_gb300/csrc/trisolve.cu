@@ -156,7 +156,9 @@ __device__ __forceinline__ void fetch_row(RowPre<B, UPPER, TV>& p, int pos, int 
 // is folded into `own` here, a turn after its operands were loaded, so that
 // neither the operands (registers) nor the FP64 product stay on the row's
 // critical path (measured: 3 % faster in FP64, 3 % slower in FP32, where the
-// product is cheap and is formed at the start of the row instead).
+// product is cheap and is formed at the start of the row instead).  Taking
+// it instead as a virtual first block [D_i^{-1} | y_i] of the row, in the
+// same FP64 instructions as the row's blocks, measured 5 % slower per CTA.
 template <int B, bool UPPER, typename TV>
 __device__ __forceinline__ void fetch_deps(RowPre<B, UPPER, TV>& p, const double* out, int lo, int hi, int lane) {
   const bool remote = p.j >= 0 && (p.j < lo || p.j >= hi);
@@ -170,13 +172,16 @@ __device__ __forceinline__ void fetch_deps(RowPre<B, UPPER, TV>& p, const double
   }
 }
 
-template <int B, bool UPPER, typename TV, int kTriWarps>
+// GE: the groups a row's blocks are spread over (a power of two, at most
+// groups_for(B)); the partial sums take log2(GE) reduction steps.
+template <int B, bool UPPER, typename TV, int kTriWarps, int GE>
 __global__ void __launch_bounds__(kTriWarps * 32) tri_solve_kernel(
     int32_t n, int32_t chunk, int32_t nchunks, const int32_t* __restrict__ bnd, const int32_t* __restrict__ rp,
     const int32_t* __restrict__ ci, const TV* __restrict__ vals, const TV* __restrict__ dinv,
     const int32_t* __restrict__ ord, const int32_t* __restrict__ tick, const double* rhs, double* out,
     int32_t* header, long long spin_ns, int32_t skip_row, int32_t* stop) {
-  constexpr int G = groups_for(B);
+  static_assert(GE >= 1 && GE <= groups_for(B) && (GE & (GE - 1)) == 0, "group count");
+  constexpr int G = GE;
   using VB = ValueBits<TV>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   TV* yl = reinterpret_cast<TV*>(smem_raw);  // the chunk's values, in the type they are used in
@@ -318,15 +323,15 @@ size_t tri_smem_bytes(int chunk, int b) {
 // Persistent grid: as many CTAs as fit on the device at once (cached per
 // shared-memory size; the occupancy query is host work worth skipping per
 // launch).
-template <int B, bool UPPER, typename TV, int kTriWarps>
+template <int B, bool UPPER, typename TV, int kTriWarps, int GE>
 int tri_grid(size_t smem, int nchunks) {
   static size_t last_smem = 0;
   static int last_per_sm = 1;
   if (smem != last_smem) {
-    cudaFuncSetAttribute(tri_solve_kernel<B, UPPER, TV, kTriWarps>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaFuncSetAttribute(tri_solve_kernel<B, UPPER, TV, kTriWarps, GE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)std::max<size_t>(smem, 48 * 1024));
     int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tri_solve_kernel<B, UPPER, TV, kTriWarps>,
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tri_solve_kernel<B, UPPER, TV, kTriWarps, GE>,
                                                   kTriWarps * 32, smem);
     last_per_sm = per_sm < 1 ? 1 : per_sm;
     last_smem = smem;
@@ -334,26 +339,61 @@ int tri_grid(size_t smem, int nchunks) {
   return std::max(1, std::min(nchunks, last_per_sm * sm_count()));
 }
 
+// One triangular solve (the arguments of tri_solve_kernel).
+template <typename TV>
+struct TriArgs {
+  int32_t n, chunk, nchunks;
+  const int32_t *bnd, *rp, *ci;
+  const TV *vals, *dinv;
+  const int32_t *ord, *tick;
+  const double* rhs;
+  double* out;
+  int32_t* header;
+  long long spin_ns;
+  int32_t skip_row;
+  int32_t* stop;
+};
+
+template <int B, bool UPPER, typename TV, int W, int GE>
+void launch_tri(const TriArgs<TV>& a, size_t smem, cudaStream_t s) {
+  const int grid = tri_grid<B, UPPER, TV, W, GE>(smem, a.nchunks);
+  tri_solve_kernel<B, UPPER, TV, W, GE><<<grid, W * 32, smem, s>>>(a.n, a.chunk, a.nchunks, a.bnd, a.rp, a.ci, a.vals,
+                                                                  a.dinv, a.ord, a.tick, a.rhs, a.out, a.header,
+                                                                  a.spin_ns, a.skip_row, a.stop);
+}
+
+// The fewest groups (a power of two, at least groups_for(B) / 4) that hold
+// every row's blocks in one pass: narrow rows (ILU(0) of a 7-point stencil:
+// 3 blocks) then take fewer reduction steps.  Only the default 4-warp CTA has
+// the narrower instantiations.
+template <int B, bool UPPER, typename TV, int W>
+void launch_tri_groups(const TriArgs<TV>& a, int32_t max_blocks, size_t smem, cudaStream_t s) {
+  constexpr int G = groups_for(B);
+  const int32_t need = max_blocks;
+  if constexpr (W == 4) {
+    if (need <= G / 4) return launch_tri<B, UPPER, TV, W, G / 4>(a, smem, s);
+    if (need <= G / 2) return launch_tri<B, UPPER, TV, W, G / 2>(a, smem, s);
+  }
+  launch_tri<B, UPPER, TV, W, G>(a, smem, s);
+}
+
 template <int B, typename TV, int W>
 void launch_solves(const bilu_pattern* p, int chunk, int nchunks, const TV* L, const TV* Dinv,
                    const TV* U, const double* r, double* y, double* x, int32_t* header, const TrisolveConfig& cfg,
                    int32_t* stop, void* stream) {
   cudaStream_t s = (cudaStream_t)stream;
-  const int32_t n = p->n;
   const size_t smem = tri_smem_bytes<TV>(chunk, B);
   {
-    const int grid = tri_grid<B, false, TV, W>(smem, nchunks);
+    const TriArgs<TV> a{p->n, chunk, nchunks, p->solve.d_bnd, p->d_lrp, p->d_lci, L, nullptr,
+                        p->solve.d_ord_l, p->solve.d_tick_l, r, y, header, cfg.spin_ns, cfg.skip_row, stop};
     ProfScope ps(BILU_PROF_LOWER, stream);
-    tri_solve_kernel<B, false, TV, W><<<grid, W * 32, smem, s>>>(n, chunk, nchunks, p->solve.d_bnd, p->d_lrp, p->d_lci, L,
-                                                                 nullptr, p->solve.d_ord_l, p->solve.d_tick_l, r, y,
-                                                                 header, cfg.spin_ns, cfg.skip_row, stop);
+    launch_tri_groups<B, false, TV, W>(a, p->max_l, smem, s);
   }
   {
-    const int grid = tri_grid<B, true, TV, W>(smem, nchunks);
+    const TriArgs<TV> a{p->n, chunk, nchunks, p->solve.d_bnd, p->d_urp, p->d_uci, U, Dinv,
+                        p->solve.d_ord_u, p->solve.d_tick_u, y, x, header, cfg.spin_ns, -1, stop};
     ProfScope ps(BILU_PROF_UPPER, stream);
-    tri_solve_kernel<B, true, TV, W><<<grid, W * 32, smem, s>>>(n, chunk, nchunks, p->solve.d_bnd, p->d_urp, p->d_uci, U, Dinv,
-                                                                p->solve.d_ord_u, p->solve.d_tick_u, y, x, header,
-                                                                cfg.spin_ns, -1, stop);
+    launch_tri_groups<B, true, TV, W>(a, p->max_u, smem, s);
   }
 }
 

@@ -95,6 +95,38 @@ def test_factor_apply_27pt(B, k):
     _check_factor_apply(B, S, k, chunks=(1, 32, 100), factor_chunks=(3, 100, 1024))
 
 
+@pytest.mark.parametrize("b", [1, 2, 3, 5, 8])
+@pytest.mark.parametrize("dims,k,width", [((300, 1, 1), 0, 1), ((17, 13, 1), 0, 2), ((9, 8, 6), 0, 3),
+                                          ((9, 8, 6), 1, 6)])
+def test_apply_row_widths(B, b, dims, k, width):
+    """Rows of at most 1, 2, 3 and 6 blocks in L and in U' (a chain, a 5-point
+    plane, a 7-point grid at ILU(0) and ILU(1)).  Each solve spreads a row over
+    the fewest block groups that hold it in one pass, so these widths run
+    every group count of every b; FP64 and FP32 applies against the oracle."""
+    S = reservoir_system(*dims, b, sigma=1.0, accum=0.01, seed=7 * b + width)
+    o = OracleRun(S.n, b, S.row_ptr, S.col_idx, S.vals, k)
+    rows = np.repeat(np.arange(S.n), np.diff(o.prp))
+    assert np.bincount(rows[o.lower], minlength=S.n).max() == width
+    assert np.bincount(rows[o.upper], minlength=S.n).max() == width
+    rp, ci, vals, rhs = device_system(S, DEV)
+    P = B.bilu_symbolic(S.n, S.row_ptr, S.col_idx, k).upload()
+    F, info = B.bilu_factor(P, b, vals)
+    assert info.status == 0
+    old = B.bilu_get_trisolve_chunk()
+    try:
+        for ch in (1, 32):
+            B.bilu_set_trisolve_chunk(ch)
+            x = B.bilu_apply(P, b, F, rhs).cpu().numpy()
+            assert rel_maxerr(x, o.apply(S.rhs)) <= TOL_APPLY, ch
+            x32 = B.bilu_apply_f32(P, b, B.bilu_convert_f32(F), rhs).cpu().numpy()
+            xo32 = oracle.apply(S.n, b, o.prp, o.pci, o.F.astype(np.float32).astype(np.float64),
+                                o.Dinv.astype(np.float32).astype(np.float64),
+                                S.rhs.astype(np.float32).astype(np.float64))
+            assert rel_maxerr(x32, xo32) <= 1e-4, ch  # FP32 arithmetic, as in the mixed-precision tests
+    finally:
+        B.bilu_set_trisolve_chunk(old)
+
+
 @pytest.mark.parametrize("seed", range(4))
 @pytest.mark.parametrize("b", [2, 3, 7])
 def test_factor_apply_random_nonsymmetric(B, seed, b):
