@@ -45,14 +45,11 @@ FP64_PEAK_TFLOPS = 1.196  # measured FP64 FMA rate of this GB300 (FMA = 2 flops)
 # DRAM bytes (read + write) per launch of a kernel, from one ncu capture of the
 # kernel as it stands (profiles/trisolve_spmv_factor_grid96x96x48_b3_k1.md holds
 # the summary and the command); keyed by (workload, k, kernel).  The capture
-# ran on the 96 x 96 x 48 case (the recipe's size rule); a solve streams each
+# runs on the 96 x 96 x 48 case (the recipe's size rule); a solve streams each
 # factor block once, so its traffic is scaled to the 128 x 128 x 64 launch by
-# the algorithmic bytes (measured traffic / algorithmic = 1.044 for the upper
-# solve, 1.048 for the lower, 0.989 for the SpMV).  Missing entries report null.
-NCU_TRAFFIC = {
-    ("grid128x128x64_7pt_b3", 1, "upper_solve"): 626915781,
-    ("grid128x128x64_7pt_b3", 1, "lower_solve"): 550252912,
-}
+# the algorithmic bytes.  Missing entries (no capture of the kernel as it
+# stands) report null.
+NCU_TRAFFIC = {}
 
 
 def parse():
@@ -95,10 +92,12 @@ def system(args):
 def algorithmic_bytes(n, b, nnz_a, nnz_l, nnz_u, v=8):
     """Bytes a kernel must move at least once (values, indices, vectors)."""
     bb = b * b
-    spmv = nnz_a * (v * bb + 4) + 4 * (n + 1) + 2 * n * b * v
-    lower = nnz_l * (v * bb + 4) + 4 * (n + 1) + 2 * n * b * v            # L, r in, y out
-    upper = nnz_u * (v * bb + 4) + n * v * bb + 4 * (n + 1) + 2 * n * b * v  # U', D^-1, y in, x out
-    return dict(spmv=spmv, lower_solve=lower, upper_solve=upper, apply=lower + upper)
+    spmv = nnz_a * (v * bb + 4) + 4 * (n + 1) + 2 * n * b * 8            # A, x in, y out (FP64 vectors)
+    lower = nnz_l * (v * bb + 4) + 4 * (n + 1) + 2 * n * b * 8            # L, r in, y out (FP64 vectors)
+    diag = n * v * bb + 2 * n * b * 8                                     # D^-1, y in, z out
+    upper = nnz_u * (v * bb + 4) + 4 * (n + 1) + 2 * n * b * 8            # U', z in, x out
+    return dict(spmv=spmv, lower_solve=lower, diag_scale=diag, upper_solve=upper,
+                apply=lower + diag + upper)
 
 
 class ClockSampler:
@@ -486,7 +485,7 @@ def main():
     ab = algorithmic_bytes(S.n, b, S.nnzb, info.nnz_l, info.nnz_u)
     hbm, peak_src = peaks()
     kern = {}
-    for name in ("spmv", "lower_solve", "upper_solve"):
+    for name in ("spmv", "lower_solve", "diag_scale", "upper_solve"):
         nl, tm = prof[name]
         if nl:
             avg_ms = tm / nl

@@ -79,7 +79,7 @@ enum bilu_prof_kernel {
   BILU_PROF_SPMV = 0,         /* bsr_spmv kernel */
   BILU_PROF_APPLY_PREP = 1,   /* apply: reset of the pending markers */
   BILU_PROF_LOWER = 2,        /* apply: sync-free L y = r */
-  BILU_PROF_UPPER = 3,        /* apply: sync-free U' x = D^{-1} y */
+  BILU_PROF_UPPER = 3,        /* apply: sync-free U' x = z (z = D^{-1} y) */
   BILU_PROF_BACKFILL = 4,     /* factor: A -> A' gather */
   BILU_PROF_FACTOR = 5,       /* factor: Algorithm 4 + D^{-1} */
   BILU_PROF_SCALE_UPPER = 6,  /* factor: U' = D^{-1} U */
@@ -87,7 +87,8 @@ enum bilu_prof_kernel {
   BILU_PROF_FACTOR_INIT = 8,  /* factor: reset of the ready flags */
   BILU_PROF_ADJOINT = 9,      /* adjoint: block gather-transposes and -lambda x^T */
   BILU_PROF_SYMBOLIC = 10,    /* device symbolic phase (bilu_symbolic_gpu) */
-  BILU_PROF_NKERNELS = 11
+  BILU_PROF_DIAG = 11,        /* apply: z = D^{-1} y between the two sweeps */
+  BILU_PROF_NKERNELS = 12
 };
 
 /* Per-kernel timing: when on, every launch of the library is bracketed by

@@ -98,7 +98,7 @@ SIGNATURES = {
 }
 
 PROF_KERNELS = ["spmv", "apply_prep", "lower_solve", "upper_solve", "backfill", "factor",
-                "scale_upper", "krylov_vector", "factor_init", "adjoint", "symbolic"]
+                "scale_upper", "krylov_vector", "factor_init", "adjoint", "symbolic", "diag_scale"]
 
 _lib = None
 

@@ -1,6 +1,13 @@
 // trisolve.cu -- preconditioner apply x = M^{-1} r, M = L D U' (Eq. 6,
-// Algorithm 7): L y = r, then U' x = D^{-1} y with the D^{-1} product fused
-// into the upper solve (row i forms D_i^{-1} y_i and subtracts U'_ij x_j).
+// Algorithm 7): L y = r, then z = D^{-1} y, then U' x = z (row i subtracts
+// U'_ij x_j from z_i).
+//
+// z = D^{-1} y is a separate pass between the two sweeps, in place over y,
+// with one lane per component: b FP64 instructions per 32/b block rows.
+// Inside the U' sweep the same product costs b FP64 instructions per row
+// (b of 32 lanes busy); FP64 issue is the scarce unit of the sweeps, and every
+// FP64 instruction taken out of them also shortens the chain of dependent
+// rows, which waits on that unit.
 //
 // The paper schedules each triangular solve by dependency levels (Eq. 4,
 // Algorithm 6), one parallel step per level.  On this part a dependent launch
@@ -95,30 +102,24 @@ __global__ void apply_prep_kernel(double* y, double* x, long long m, int32_t* he
   }
 }
 
-template <typename TV>
-constexpr bool kFoldOwn = sizeof(TV) == 8;  // see fetch_deps
-
 // Registers a lane holds for one row: the row, its first block of this lane's
-// group (column, this lane's B values, optimistic dependency values), and what
-// the row's own update needs (r_i for L; D_i^{-1} row and y_i for U').
-template <int B, bool UPPER, typename TV>
+// group (column, this lane's B values, optimistic dependency values), and the
+// row's own term (r_i for L, z_i for U').
+template <int B, typename TV>
 struct RowPre {
   int i, beg, end, j;
   TV av[B];
   unsigned long long yv[B];  // dependency values of a block outside the chunk, read early
-  double own;                // L: r_i[lane]; U': (D_i^{-1} y_i)[lane] once folded
-  TV d[B];                   // U': D_i^{-1}[lane][q]  (until folded into own)
-  double yi[B];              // U': y_i[q]             (until folded into own)
+  double own;                // lanes < B: r_i[lane] or z_i[lane]
 };
 
 // Stage A of the prefetch: the row, its first block (column and values) and
-// its own operands.
-template <int B, bool UPPER, typename TV>
-__device__ __forceinline__ void fetch_row(RowPre<B, UPPER, TV>& p, int pos, int len, const int* s_i,
+// its own term.
+template <int B, typename TV>
+__device__ __forceinline__ void fetch_row(RowPre<B, TV>& p, int pos, int len, const int* s_i,
                                           const int* s_beg, const int* s_end,
                                           const int32_t* __restrict__ ci, const TV* __restrict__ vals,
-                                          const TV* __restrict__ dinv, const double* rhs, int g, int rr,
-                                          bool act, int lane) {
+                                          const double* rhs, int g, int rr, bool act, int lane) {
   if (pos >= len) {  // past the chunk's end: nothing to fetch, no dependency to read
     p.i = -1;
     p.beg = p.end = 0;
@@ -136,40 +137,46 @@ __device__ __forceinline__ void fetch_row(RowPre<B, UPPER, TV>& p, int pos, int 
 #pragma unroll
     for (int q = 0; q < B; ++q) p.av[q] = __ldg(a + q * B);
   }
-  if (lane < B) {
-    if (!UPPER) {
-      p.own = rhs[(size_t)p.i * B + lane];
-    } else {
-      const TV* di = dinv + (size_t)p.i * (B * B) + lane;
-#pragma unroll
-      for (int q = 0; q < B; ++q) {
-        p.d[q] = __ldg(di + q * B);
-        p.yi[q] = rhs[(size_t)p.i * B + q];
-      }
-    }
-  }
+  if (lane < B) p.own = rhs[(size_t)p.i * B + lane];
 }
 
 // Stage B: a dependency outside the chunk is usually final already: read it
 // now (relaxed); if it still holds the pending pattern it is waited for later.
-// For U' the row's own term D_i^{-1} y_i depends on no other row.  In FP64 it
-// is folded into `own` here, a turn after its operands were loaded, so that
-// neither the operands (registers) nor the FP64 product stay on the row's
-// critical path (measured: 3 % faster in FP64, 3 % slower in FP32, where the
-// product is cheap and is formed at the start of the row instead).  Taking
-// it instead as a virtual first block [D_i^{-1} | y_i] of the row, in the
-// same FP64 instructions as the row's blocks, measured 5 % slower per CTA.
-template <int B, bool UPPER, typename TV>
-__device__ __forceinline__ void fetch_deps(RowPre<B, UPPER, TV>& p, const double* out, int lo, int hi, int lane) {
+template <int B, typename TV>
+__device__ __forceinline__ void fetch_deps(RowPre<B, TV>& p, const double* out, int lo, int hi) {
   const bool remote = p.j >= 0 && (p.j < lo || p.j >= hi);
 #pragma unroll
   for (int q = 0; q < B; ++q) p.yv[q] = remote ? ld_relaxed_u64(out + (size_t)p.j * B + q) : kPending;
-  if (UPPER && kFoldOwn<TV> && lane < B) {
-    TV z = TV(0);
+}
+
+// z = D^{-1} y in place: R = 32 / B block rows per warp, lane (row, r) forms
+// z[row][r] = sum_c D^{-1}[r][c] y[row][c] (blocks column-major).  A row's
+// lanes sit in one warp; they read all of y_row before any of them writes.
+template <int B, typename TV>
+__global__ void __launch_bounds__(256) diag_scale_kernel(int32_t n, const TV* __restrict__ dinv, double* y,
+                                                         const int32_t* stop) {
+  constexpr int R = 32 / B;
+  if (stop && ld_volatile_s32(stop)) return;
+  const int lane = threadIdx.x & 31;
+  const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int q = lane / B;
+  const int r = lane - q * B;
+  const long long row = warp * R + q;
+  const bool act = q < R && row < n;
+  TV z = TV(0);
+  if (act) {
+    const TV* d = dinv + (size_t)row * (B * B) + r;
+    const double* yr = y + (size_t)row * B;
 #pragma unroll
-    for (int q = 0; q < B; ++q) z = fma(p.d[q], (TV)p.yi[q], z);
-    p.own = (double)z;
+    for (int c = 0; c < B; ++c) {
+      TV yc;
+      if constexpr (sizeof(TV) == 4) yc = d2f_rn(yr[c]);
+      else yc = yr[c];
+      z = fma(__ldg(d + c * B), yc, z);
+    }
   }
+  __syncwarp();
+  if (act) y[(size_t)row * B + r] = (double)z;
 }
 
 // GE: the groups a row's blocks are spread over (a power of two, at most
@@ -177,7 +184,7 @@ __device__ __forceinline__ void fetch_deps(RowPre<B, UPPER, TV>& p, const double
 template <int B, bool UPPER, typename TV, int kTriWarps, int GE>
 __global__ void __launch_bounds__(kTriWarps * 32) tri_solve_kernel(
     int32_t n, int32_t chunk, int32_t nchunks, const int32_t* __restrict__ bnd, const int32_t* __restrict__ rp,
-    const int32_t* __restrict__ ci, const TV* __restrict__ vals, const TV* __restrict__ dinv,
+    const int32_t* __restrict__ ci, const TV* __restrict__ vals,
     const int32_t* __restrict__ ord, const int32_t* __restrict__ tick, const double* rhs, double* out,
     int32_t* header, long long spin_ns, int32_t skip_row, int32_t* stop) {
   static_assert(GE >= 1 && GE <= groups_for(B) && (GE & (GE - 1)) == 0, "group count");
@@ -217,30 +224,19 @@ __global__ void __launch_bounds__(kTriWarps * 32) tri_solve_kernel(
     }
     for (int q = tid; q < len * B; q += blockDim.x) reinterpret_cast<typename VB::U*>(yl)[q] = VB::kPend;
     __syncthreads();
-    RowPre<B, UPPER, TV> cur, nx1, nx2;
-    fetch_row<B, UPPER, TV>(cur, warp, len, s_i, s_beg, s_end, ci, vals, dinv, rhs, g, rr, act, lane);
-    fetch_deps<B, UPPER, TV>(cur, out, lo, hi, lane);
-    fetch_row<B, UPPER, TV>(nx1, warp + kTriWarps, len, s_i, s_beg, s_end, ci, vals, dinv, rhs, g, rr, act,
-                            lane);
+    RowPre<B, TV> cur, nx1, nx2;
+    fetch_row<B, TV>(cur, warp, len, s_i, s_beg, s_end, ci, vals, rhs, g, rr, act, lane);
+    fetch_deps<B, TV>(cur, out, lo, hi);
+    fetch_row<B, TV>(nx1, warp + kTriWarps, len, s_i, s_beg, s_end, ci, vals, rhs, g, rr, act, lane);
     for (int pos = warp; pos < len && !dead; pos += kTriWarps) {
-      fetch_row<B, UPPER, TV>(nx2, pos + 2 * kTriWarps, len, s_i, s_beg, s_end, ci, vals, dinv, rhs, g, rr,
-                              act, lane);
-      fetch_deps<B, UPPER, TV>(nx1, out, lo, hi, lane);
+      fetch_row<B, TV>(nx2, pos + 2 * kTriWarps, len, s_i, s_beg, s_end, ci, vals, rhs, g, rr, act, lane);
+      fetch_deps<B, TV>(nx1, out, lo, hi);
       const int i = cur.i;
       bool ok = true;
-      // The row's own term in TV, formed before the waits (FP32 U': D_i^{-1} y_i
-      // here), seeds the sum of group 0 (lanes < B); the blocks then accumulate
-      // as fma(-a, y, acc), so the reduced sum is the row's value with no final
-      // subtraction (one FP64 instruction and its latency fewer per row).
-      TV acc = TV(0);
-      if (lane < B) {
-        if (UPPER && !kFoldOwn<TV>) {
-#pragma unroll
-          for (int q = 0; q < B; ++q) acc = fma(cur.d[q], (TV)cur.yi[q], acc);
-        } else {
-          acc = (TV)cur.own;
-        }
-      }
+      // The row's own term (r_i or z_i) seeds the sum of group 0 (lanes < B);
+      // the blocks accumulate as fma(-a, y, acc), so the reduced sum is the
+      // row's value with no final subtraction.
+      TV acc = lane < B ? (TV)cur.own : TV(0);
       for (int t0 = cur.beg; t0 < cur.end; t0 += G) {
         const int t = t0 + g;
         if (act && t < cur.end) {
@@ -344,7 +340,7 @@ template <typename TV>
 struct TriArgs {
   int32_t n, chunk, nchunks;
   const int32_t *bnd, *rp, *ci;
-  const TV *vals, *dinv;
+  const TV* vals;
   const int32_t *ord, *tick;
   const double* rhs;
   double* out;
@@ -358,7 +354,7 @@ template <int B, bool UPPER, typename TV, int W, int GE>
 void launch_tri(const TriArgs<TV>& a, size_t smem, cudaStream_t s) {
   const int grid = tri_grid<B, UPPER, TV, W, GE>(smem, a.nchunks);
   tri_solve_kernel<B, UPPER, TV, W, GE><<<grid, W * 32, smem, s>>>(a.n, a.chunk, a.nchunks, a.bnd, a.rp, a.ci, a.vals,
-                                                                  a.dinv, a.ord, a.tick, a.rhs, a.out, a.header,
+                                                                  a.ord, a.tick, a.rhs, a.out, a.header,
                                                                   a.spin_ns, a.skip_row, a.stop);
 }
 
@@ -384,13 +380,22 @@ void launch_solves(const bilu_pattern* p, int chunk, int nchunks, const TV* L, c
   cudaStream_t s = (cudaStream_t)stream;
   const size_t smem = tri_smem_bytes<TV>(chunk, B);
   {
-    const TriArgs<TV> a{p->n, chunk, nchunks, p->solve.d_bnd, p->d_lrp, p->d_lci, L, nullptr,
+    const TriArgs<TV> a{p->n, chunk, nchunks, p->solve.d_bnd, p->d_lrp, p->d_lci, L,
                         p->solve.d_ord_l, p->solve.d_tick_l, r, y, header, cfg.spin_ns, cfg.skip_row, stop};
     ProfScope ps(BILU_PROF_LOWER, stream);
     launch_tri_groups<B, false, TV, W>(a, p->max_l, smem, s);
   }
   {
-    const TriArgs<TV> a{p->n, chunk, nchunks, p->solve.d_bnd, p->d_urp, p->d_uci, U, Dinv,
+    // z = D^{-1} y over y.  A lower sweep that gave up (a bounded wait ran
+    // out) leaves pending slots in y: they turn into NaN here, and the upper
+    // sweep, whose header shows the abort, leaves at once.
+    constexpr int R = 32 / B;
+    const long long blocks = (((long long)p->n + R - 1) / R * 32 + 255) / 256;
+    ProfScope ps(BILU_PROF_DIAG, stream);
+    diag_scale_kernel<B, TV><<<(unsigned)blocks, 256, 0, s>>>(p->n, Dinv, y, stop);
+  }
+  {
+    const TriArgs<TV> a{p->n, chunk, nchunks, p->solve.d_bnd, p->d_urp, p->d_uci, U,
                         p->solve.d_ord_u, p->solve.d_tick_u, y, x, header, cfg.spin_ns, -1, stop};
     ProfScope ps(BILU_PROF_UPPER, stream);
     launch_tri_groups<B, true, TV, W>(a, p->max_u, smem, s);
