@@ -183,3 +183,33 @@ def test_convert_f32_bit_exact_on_many_values(B):
     with np.errstate(over="ignore"):
         ref = x.astype(np.float32)
     assert np.array_equal(got.view(np.uint32), ref.view(np.uint32))
+
+
+def test_apply_f32_conversions_bit_exact(B):
+    """FP32 apply on a b = 1 block-diagonal system: x_i = double(float(d_i *
+    float(r_i))), one rounding of one product, so every conversion on the way
+    (r to float, y and z through the FP64 vectors and back, x to double) must
+    be exact or correctly rounded: the result equals numpy bit for bit.  The
+    values span 60 decades, with zeros of both signs, products that underflow
+    to float subnormals and products that overflow to infinity."""
+    rng = np.random.default_rng(11)
+    n = 200_000
+    r = rng.standard_normal(n) * 10.0 ** rng.integers(-20, 20, n)
+    r[:1000] = 0.0
+    r[1000:2000] = -0.0
+    a = rng.choice([-1.0, 1.0], n) * rng.uniform(0.5, 2.0, n) * 10.0 ** rng.integers(-10, 10, n)
+    r[2000:2100], a[2000:2100] = 1e-30, 1e12       # |d r| ~ 1e-42: float subnormal
+    r[2100:2200], a[2100:2200] = -3e25, -1e-16     # |d r| ~ 3e41: float infinity
+    rp = np.arange(n + 1, dtype=np.int32)
+    ci = np.arange(n, dtype=np.int32)
+    P = B.bilu_symbolic(n, rp, ci, 0).upload()
+    F, info = B.bilu_factor(P, 1, torch.from_numpy(a).to(DEV))
+    assert info.status == 0
+    F32 = B.bilu_convert_f32(F)
+    x = B.bilu_apply_f32(P, 1, F32, torch.from_numpy(r).to(DEV)).cpu().numpy()
+    d32 = F32.cpu().numpy()
+    with np.errstate(over="ignore", under="ignore"):
+        z = d32 * r.astype(np.float32) + np.float32(0.0)  # fma(d, r, +0): a zero product is +0
+    ref = z.astype(np.float64)
+    assert np.array_equal(x.view(np.uint64), ref.view(np.uint64))
+    assert np.isinf(ref[2100:2200]).all() and (np.abs(ref[2000:2100]) < 1.2e-38).all()
