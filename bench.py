@@ -49,7 +49,12 @@ FP64_PEAK_TFLOPS = 1.196  # measured FP64 FMA rate of this GB300 (FMA = 2 flops)
 # factor block once, so its traffic is scaled to the 128 x 128 x 64 launch by
 # the algorithmic bytes.  Missing entries (no capture of the kernel as it
 # stands) report null.
-NCU_TRAFFIC = {}
+NCU_TRAFFIC = {
+    ("grid128x128x64_7pt_b3", 1, "upper_solve"): 550966852,   # 1.049 x algorithmic
+    ("grid128x128x64_7pt_b3", 1, "lower_solve"): 551877719,   # 1.051 x
+    ("grid128x128x64_7pt_b3", 1, "diag_scale"): 100672398,    # 0.800 x (z stays in L2)
+    ("grid128x128x64_7pt_b3", 1, "spmv"): 600628668,          # 0.989 x
+}
 
 
 def parse():
