@@ -72,6 +72,9 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-precision", action="store_true", help="skip the FP32-preconditioner comparison")
+    ap.add_argument("--sweep", choices=["c2", "c3"], default=None,
+                    help="instead of the bench line: one JSON line per configuration of the 96 x 96 x 48 "
+                         "b x k sweep (c2) or of the 160 x 160 x 80 27-point ILU(2) case (c3)")
     ap.add_argument("--no-extras", action="store_true",
                     help="time the step only (no small-case, FP32-kernel or precision sections)")
     return ap.parse_args()
@@ -416,10 +419,107 @@ def fp32_kernel_rates(B, S, P, F, vals, rhs, rp, ci, dev, stream, reps=10):
     return res
 
 
+def sweep(B, dev, stream, which, tol=1e-8, reps=20):
+    """Per-configuration numbers, one JSON line each: the device symbolic
+    phase, FP64 and FP32 factorization, FP64 and FP32 apply and SpMV (mean
+    CUDA-event time over `reps` calls, algorithmic GB/s), and BiCGSTAB from
+    x0 = 0 to a true relative residual of `tol` with the FP64 preconditioner
+    and with the FP32-stored one (median of `solve_reps` solves, factorization
+    excluded).  Inputs are larger than L2 in every configuration.  The
+    160 x 160 x 80 case reaches 1e-8 in neither precision: its solves run a
+    300-iteration budget once and report where they stand."""
+    import torch
+    from paper_1703_01325_gb300.reservoir import WORKLOADS, reservoir_system
+    if which == "c2":
+        cases = [("grid96x96x48_7pt", b, k) for b in (2, 4, 6, 8) for k in (0, 1, 2)]
+        maxit, solve_reps = 5000, 3
+    else:
+        cases = [("grid160x160x80_27pt_b3", 3, 2)]
+        maxit, solve_reps = 300, 1
+    hbm, _ = peaks()
+
+    def timed(fn, n):
+        fn()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(n):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / n
+
+    for wl, b, k in cases:
+        cfg = dict(WORKLOADS[wl])
+        cfg["b"] = b
+        S = reservoir_system(**cfg)
+        t0 = time.perf_counter()
+        P = B.bilu_symbolic_gpu(S.n, S.row_ptr, S.col_idx, k)
+        sym_ms = (time.perf_counter() - t0) * 1e3
+        P.upload()
+        info = P.info
+        rp, ci = torch.from_numpy(S.row_ptr).to(dev), torch.from_numpy(S.col_idx).to(dev)
+        vals, rhs = torch.from_numpy(S.vals.reshape(-1)).to(dev), torch.from_numpy(S.rhs).to(dev)
+        A = (S.n, b, rp, ci, vals)
+        F = B.new_factors(P, b, dev)
+        F32 = torch.empty(max(P.factor_bytes_f32(b) // 4, 1), dtype=torch.float32, device=dev)
+        fw = B.workspace(P.factor_workspace_bytes(b), dev)
+        aw = B.workspace(P.apply_workspace_bytes(b), dev)
+        sw = B.workspace(P.bicgstab_workspace_bytes(b), dev)
+        V32 = B.bilu_convert_f32(vals)
+        x, y = torch.empty_like(rhs), torch.empty_like(rhs)
+        row = {"workload": wl, "b": b, "k": k, "n": S.n, "nnzb": S.nnzb, "nnz_l": info.nnz_l,
+               "nnz_u": info.nnz_u, "levels_lower": info.nlev_l, "symbolic_gpu_ms": round(sym_ms, 1)}
+        row["factor_ms"] = round(timed(lambda: B.bilu_factor(P, b, vals, F, fw), 3), 2)
+        row["factor_f32_ms"] = round(timed(lambda: B.bilu_factor_f32(P, b, vals, F32, fw), 3), 2)
+        B.bilu_factor(P, b, vals, F, fw)
+        B.bilu_convert_f32(F, F32)
+        for v, tag in ((8, "f64"), (4, "f32")):
+            ab = algorithmic_bytes(S.n, b, S.nnzb, info.nnz_l, info.nnz_u, v=v)
+            if tag == "f64":
+                fa = lambda: B.bilu_apply(P, b, F, rhs, x, aw)
+                fs = lambda: B.bsr_spmv(S.n, b, rp, ci, vals, rhs, y)
+            else:
+                fa = lambda: B.bilu_apply_f32(P, b, F32, rhs, x, aw)
+                fs = lambda: B.bsr_spmv_f32(S.n, b, rp, ci, V32, rhs, y)
+            for name, fn, by in (("apply", fa, ab["apply"]), ("spmv", fs, ab["spmv"])):
+                ms = timed(fn, reps)
+                gbs = by / (ms * 1e-3) / 1e9
+                row[f"{name}_{tag}"] = {"us": round(ms * 1e3, 1), "gbs": round(gbs, 1), "frac_hbm": round(gbs / hbm, 3)}
+        for tag, fac in (("bicgstab_f64", None), ("bicgstab_f32prec", F32)):
+            runs = []
+            for _ in range(solve_reps):
+                x.zero_()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                torch.cuda.synchronize()
+                e0.record(stream)
+                if fac is None:
+                    si = B.bicgstab_solve(P, A, F, rhs, x=x, tol=tol, maxit=maxit, work=sw)[1]
+                else:
+                    si = B.bicgstab_solve_f32prec(P, A, F32, rhs, x=x, tol=tol, maxit=maxit, work=sw)[1]
+                e1.record(stream)
+                torch.cuda.synchronize()
+                runs.append((e0.elapsed_time(e1), si))
+            runs.sort(key=lambda r: r[0])
+            ms, si = runs[len(runs) // 2]
+            row[tag] = {"ms": round(ms, 2), "iters": si.iters, "true_relres": si.true_relres, "status": si.status}
+        print(json.dumps(row), flush=True)
+        del F, F32, fw, aw, sw, V32, vals
+        P.close()
+        torch.cuda.empty_cache()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.sweep:
+        import torch
+        import paper_1703_01325_gb300.bilu as B
+        dev = torch.device("cuda:0")
+        torch.cuda.set_device(dev)
+        sweep(B, dev, torch.cuda.current_stream(dev), args.sweep)
         return
     import numpy as np
     import torch
