@@ -165,16 +165,16 @@ int bilu_factor(const bilu_pattern* p, int32_t b, const double* d_a_vals, double
 /* Preconditioner apply (device)                                             */
 /* ------------------------------------------------------------------------ */
 
-/* Scratch bytes bilu_apply needs (the intermediate y = L^{-1} r and counters). */
+/* Scratch bytes bilu_apply needs (the intermediate y = L^{-1} r, overwritten
+ * by z = D^{-1} y, and counters). */
 size_t bilu_apply_workspace_bytes(const bilu_pattern* p, int32_t b);
 
 /*
  * bilu_apply -- x = M^{-1} r with M = L D U' (Eq. 6, Algorithm 7):
  *   L y = r (rows ascending), z = D^{-1} y, U' x = z (rows descending).
- * The D^{-1} product is fused into the U' solve (row i forms D_i^{-1} y_i
- * before subtracting U'_ij x_j).  Both triangular solves run as single
- * sync-free kernels: each row waits, with a bounded spin, for the rows it
- * depends on.
+ * z = D^{-1} y is a pass of its own between the two solves, in place in the
+ * workspace.  Both triangular solves run as single sync-free kernels: each
+ * row waits, with a bounded spin, for the rows it depends on.
  *   d_factors  device, output of bilu_factor with the same b
  *   d_r, d_x   device, n*b doubles each; must not alias
  *   d_work     device scratch of at least bilu_apply_workspace_bytes bytes
