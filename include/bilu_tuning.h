@@ -26,7 +26,7 @@ int bilu_set_trisolve_chunk(int32_t rows);
 int32_t bilu_get_trisolve_chunk(void);
 
 /* Target of consecutive block rows one CTA owns in the sync-free
- * factorization: 0 (the default) picks n / (2 * SMs) clamped to [64, 512];
+ * factorization: 0 (the default) picks n / (2 * SMs) clamped to [64, 256];
  * 1 <= rows <= 1024 fixes it; other values: BILU_ERR_ARG.  Its schedule is
  * separate from the solves' and is rebuilt by the next factorization. */
 int bilu_set_factor_chunk(int32_t rows);

@@ -79,7 +79,7 @@ int32_t factor_chunk_target(int32_t n) {
   const int c = trisolve_config().factor_chunk;
   if (c > 0) return c;
   const long long t = (long long)n / (2LL * device_sm_count());
-  return (int32_t)std::max(64LL, std::min(512LL, t));
+  return (int32_t)std::max(64LL, std::min(256LL, t));
 }
 
 namespace {
