@@ -38,7 +38,9 @@
 //    leaves the CTA's chunk loop early, so no barrier can hang.
 // Lane mapping inside a row: lane = g*B + r, r the output component, g one of
 // G groups that take the row's blocks round-robin; each lane does B FMAs per
-// block and a log2(G)-step shuffle tree sums the groups.
+// block and a log2(G)-step shuffle tree sums the groups.  G is a template
+// parameter picked at launch: the fewest groups that hold the triangle's
+// widest row in one pass (at least a quarter of the 32 / B lanes' groups).
 //
 // TV is the type the factors are stored and applied in: double, or float for
 // the mixed-precision solver (vectors stay double; each value read is
