@@ -75,6 +75,8 @@ def parse():
     ap.add_argument("--sweep", choices=["c2", "c3"], default=None,
                     help="instead of the bench line: one JSON line per configuration of the 96 x 96 x 48 "
                          "b x k sweep (c2) or of the 160 x 160 x 80 27-point ILU(2) case (c3)")
+    ap.add_argument("--oracle", action="store_true",
+                    help="with --sweep c2: add the CPU oracle's kernel times (one call each, one thread)")
     ap.add_argument("--no-extras", action="store_true",
                     help="time the step only (no small-case, FP32-kernel or precision sections)")
     return ap.parse_args()
@@ -195,6 +197,26 @@ def cpu_baseline(S, k, gpu_iters, sample_iters=4):
             "sample": (f"oracle factorization of the full matrix ({factor_ms:.0f} ms) + {sample_iters} "
                        f"BiCGSTAB iterations ({per_it * 1e3:.0f} ms each), scaled to {gpu_iters} iterations; "
                        f"symbolic {1e3 * (t1 - t0):.0f} ms not counted")}
+
+
+def oracle_kernel_times(S, k):
+    """One call of each CPU oracle kernel (single thread) on the full system:
+    symbolic phase, backfill + factorization, SpMV, apply."""
+    import oracle
+    t0 = time.perf_counter()
+    prp, pci, _ = oracle.symbolic(S.n, S.row_ptr, S.col_idx, k)
+    t1 = time.perf_counter()
+    A1 = oracle.backfill(S.n, S.b, S.row_ptr, S.col_idx, S.vals, prp, pci)
+    F, D = oracle.factor(S.n, S.b, prp, pci, A1)
+    t2 = time.perf_counter()
+    oracle.spmv(S.n, S.b, S.row_ptr, S.col_idx, S.vals, S.rhs)
+    t3 = time.perf_counter()
+    oracle.apply(S.n, S.b, prp, pci, F, D, S.rhs)
+    t4 = time.perf_counter()
+    return {"kind": "oracle", "cores": 1, "cpu_model": cpu_model(), "nproc": os.cpu_count(),
+            "kernels_ms": {"symbolic": round(1e3 * (t1 - t0), 1), "factor": round(1e3 * (t2 - t1), 1),
+                           "spmv": round(1e3 * (t3 - t2), 1), "apply": round(1e3 * (t4 - t3), 1)},
+            "sample": "one call of each oracle kernel on the full system"}
 
 
 def cpu_model() -> str:
@@ -419,7 +441,7 @@ def fp32_kernel_rates(B, S, P, F, vals, rhs, rp, ci, dev, stream, reps=10):
     return res
 
 
-def sweep(B, dev, stream, which, tol=1e-8, reps=20):
+def sweep(B, dev, stream, which, tol=1e-8, reps=20, with_oracle=False):
     """Per-configuration numbers, one JSON line each: the device symbolic
     phase, FP64 and FP32 factorization, FP64 and FP32 apply and SpMV (mean
     CUDA-event time over `reps` calls, algorithmic GB/s), and BiCGSTAB from
@@ -503,6 +525,8 @@ def sweep(B, dev, stream, which, tol=1e-8, reps=20):
             runs.sort(key=lambda r: r[0])
             ms, si = runs[len(runs) // 2]
             row[tag] = {"ms": round(ms, 2), "iters": si.iters, "true_relres": si.true_relres, "status": si.status}
+        if with_oracle and which == "c2":
+            row["cpu_baseline"] = oracle_kernel_times(S, k)
         print(json.dumps(row), flush=True)
         del F, F32, fw, aw, sw, V32, vals
         P.close()
@@ -519,7 +543,7 @@ def main():
         import paper_1703_01325_gb300.bilu as B
         dev = torch.device("cuda:0")
         torch.cuda.set_device(dev)
-        sweep(B, dev, torch.cuda.current_stream(dev), args.sweep)
+        sweep(B, dev, torch.cuda.current_stream(dev), args.sweep, with_oracle=args.oracle)
         return
     import numpy as np
     import torch
