@@ -682,7 +682,7 @@ def main():
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": args.workload, "k": args.k, "tol": args.tol, "maxit": args.maxit, **cfg,
                    "n": S.n, "nnzb": S.nnzb, "nnz_p": info.nnz_p, "levels_lower": info.nlev_l,
-                   "trisolve_chunk": B.bilu_get_trisolve_chunk() or "auto (256 rows at this size)",
+                   "trisolve_chunk": B.bilu_get_trisolve_chunk() or "auto (two grid lines on natural-order grids)",
                    "l2": "inputs larger than L2 (A values %.0f MB, factors %.0f MB)" % (
                        S.nnzb * b * b * 8 / 1e6, P.factor_bytes(b) / 1e6),
                    "step": "backfill + factor + BiCGSTAB from x0 = 0 toward tol, at most maxit iterations"},

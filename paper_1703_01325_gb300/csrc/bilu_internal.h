@@ -96,7 +96,7 @@ struct TrisolveConfig {
 };
 TrisolveConfig& trisolve_config();
 // The chunk targets in effect for a system of n block rows: the configured
-// ones, or (0) n / (10 * SMs) in [32, 256] for the solves and n / (2 * SMs) in
+// ones, or (0) n / (10 * SMs) in [32, 200] for the solves and n / (2 * SMs) in
 // [64, 256] for the factorization -- enough chunks to fill the GPU.
 int32_t solve_chunk_target(int32_t n);
 int32_t factor_chunk_target(int32_t n);

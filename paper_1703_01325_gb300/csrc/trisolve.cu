@@ -74,7 +74,7 @@ int32_t solve_chunk_target(int32_t n) {
   const int c = trisolve_config().chunk;
   if (c > 0) return c;
   const long long t = (long long)n / (10LL * device_sm_count());
-  return (int32_t)std::max(32LL, std::min(256LL, t));
+  return (int32_t)std::max(32LL, std::min(200LL, t));
 }
 
 int32_t factor_chunk_target(int32_t n) {
