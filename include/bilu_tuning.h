@@ -18,14 +18,20 @@ extern "C" {
 /* Target of consecutive block rows one CTA owns in the sync-free triangular
  * solves.  Dependencies inside a chunk resolve through shared memory,
  * dependencies across chunks through global memory.  0 (the default) picks
- * per pattern: n / (10 * SMs) rows, clamped to [32, 200], so that small
- * systems still spread over the GPU and large grids get chunks of two grid
- * lines (the cut goes to the line start nearest the target: 256 rows on a
- * 128-wide grid, 192 on a 96-wide one); 1 <= rows <= 1024 fixes the target;
+ * per pattern: n / (10 * SMs) rows, clamped to [32, 256], so that small
+ * systems still spread over the GPU; where that hits 256 and the pattern
+ * shows a line length L of 16..192 rows (the most common distance between
+ * rows that do not depend on their predecessor: grid-line starts in a
+ * natural ordering), 2 L instead -- two grid lines per chunk; 1 <= rows <=
+ * 1024 fixes the target;
  * other values: BILU_ERR_ARG.  The schedule is rebuilt (host work plus one
  * device allocation) by the next apply or solve on each pattern. */
 int bilu_set_trisolve_chunk(int32_t rows);
 int32_t bilu_get_trisolve_chunk(void);
+
+/* The target the solves use for pattern p when none is set (bilu_set_trisolve_chunk(0)),
+ * for inspection: host pattern, no device work.  Returns -1 for a NULL p. */
+int32_t bilu_auto_trisolve_chunk(const bilu_pattern* p);
 
 /* Target of consecutive block rows one CTA owns in the sync-free
  * factorization: 0 (the default) picks n / (2 * SMs) clamped to [64, 256];

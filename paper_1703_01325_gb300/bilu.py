@@ -403,6 +403,11 @@ def bilu_get_trisolve_chunk() -> int:
     return int(L.load().bilu_get_trisolve_chunk())
 
 
+def bilu_auto_trisolve_chunk(P: "Pattern") -> int:
+    """The chunk target the solves use for P when none is set."""
+    return int(L.load().bilu_auto_trisolve_chunk(P.handle))
+
+
 def bilu_set_factor_chunk(rows: int):
     _check(L.load().bilu_set_factor_chunk(rows), "bilu_set_factor_chunk")
 

@@ -18,7 +18,7 @@ bool valid_b(int32_t b) { return b >= 1 && b <= 8; }
 // The schedules the factorization and the solves run on, rebuilt (host work
 // plus one device allocation) when the chunk target changed.
 int solve_schedule(const bilu_pattern* p) {
-  return ensure_schedule(p, &const_cast<bilu_pattern*>(p)->solve, solve_chunk_target(p->n), true);
+  return ensure_schedule(p, &const_cast<bilu_pattern*>(p)->solve, solve_chunk_target(p), true);
 }
 int factor_schedule(const bilu_pattern* p) {
   return ensure_schedule(p, &const_cast<bilu_pattern*>(p)->fact, factor_chunk_target(p->n), false);
@@ -101,7 +101,7 @@ extern "C" int bilu_pattern_upload(bilu_pattern* p, void* stream) {
   }
   p->d_mem = mem;
   p->device = dev;
-  if (ensure_schedule(p, &p->solve, solve_chunk_target(p->n), true) != 0 ||
+  if (ensure_schedule(p, &p->solve, solve_chunk_target(p), true) != 0 ||
       (!p->is_transpose && ensure_schedule(p, &p->fact, factor_chunk_target(p->n), false) != 0))
     return BILU_ERR_OOM;
   return BILU_OK;
@@ -395,6 +395,10 @@ extern "C" int bilu_set_factor_chunk(int32_t rows) {
 }
 
 extern "C" int32_t bilu_get_factor_chunk(void) { return trisolve_config().factor_chunk; }
+
+extern "C" int32_t bilu_auto_trisolve_chunk(const bilu_pattern* p) {
+  return p ? auto_solve_chunk_target(p) : -1;
+}
 
 extern "C" int bilu_set_trisolve_warps(int32_t warps) {
   if (warps != 4 && warps != 8 && warps != 16) return BILU_ERR_ARG;

@@ -43,6 +43,10 @@ struct bilu_pattern {
   // Strictly lower / strictly upper parts of P' as separate CSR structures.
   std::vector<int32_t> lrp, lci, urp, uci;
   int32_t max_l = 0, max_u = 0;  // most blocks in a row of L / of U'
+  // The most common distance between consecutive rows that do not depend on
+  // their predecessor (grid-line starts in a natural ordering: the line
+  // length); 0 if no distance recurs.
+  int32_t line_len = 0;
   // Backfill gather map: for every factor slot in [L | D | U] the A block that
   // lands there, or -1 for a fill block (Algorithm 5 steps 3-4).  For a
   // transposed pattern (is_transpose): the slot of the source pattern's factor
@@ -96,9 +100,12 @@ struct TrisolveConfig {
 };
 TrisolveConfig& trisolve_config();
 // The chunk targets in effect for a system of n block rows: the configured
-// ones, or (0) n / (10 * SMs) in [32, 200] for the solves and n / (2 * SMs) in
+// ones, or (0) n / (10 * SMs) in [32, 256] for the solves -- two grid lines
+// instead where that rule hits its cap and a line length of 16..192 rows is
+// detected -- and n / (2 * SMs) in
 // [64, 256] for the factorization -- enough chunks to fill the GPU.
-int32_t solve_chunk_target(int32_t n);
+int32_t solve_chunk_target(const bilu_pattern* p);
+int32_t auto_solve_chunk_target(const bilu_pattern* p);  // the rule alone
 int32_t factor_chunk_target(int32_t n);
 
 // Brackets one kernel launch with profiling events (when enabled) and counts it.

@@ -72,7 +72,7 @@ void finish_pattern(bilu_pattern* p) {
   p->nlev_u = mu + 1;
 
   // Split P' into strictly lower and strictly upper CSR structures.
-  p->max_l = p->max_u = 0;
+  p->max_l = p->max_u = p->line_len = 0;
   p->lrp.assign((size_t)n + 1, 0);
   p->urp.assign((size_t)n + 1, 0);
   for (int32_t i = 0; i < n; ++i) {
@@ -95,6 +95,21 @@ void finish_pattern(bilu_pattern* p) {
       else if (p->ci[t] > i) p->uci[c++] = p->ci[t];
     }
   }
+
+  // Line length: the most common distance (up to 4096) between consecutive
+  // rows that do not depend on row i - 1.
+  std::vector<int32_t> hist(4097, 0);
+  int32_t prev = -1;
+  for (int32_t i = 0; i < n; ++i) {
+    const int32_t e = p->lrp[(size_t)i + 1];
+    if (e > p->lrp[i] && p->lci[(size_t)e - 1] == i - 1) continue;  // depends on its predecessor
+    if (prev >= 0 && i - prev <= 4096) ++hist[(size_t)(i - prev)];
+    prev = i;
+  }
+  int32_t best = 0;
+  for (int32_t d = 2; d <= 4096; ++d)
+    if (hist[(size_t)d] > hist[(size_t)best] && hist[(size_t)d] >= 2) best = d;
+  p->line_len = best;
 }
 
 }  // namespace

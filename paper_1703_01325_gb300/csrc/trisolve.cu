@@ -70,11 +70,20 @@ int device_sm_count() {
 }
 }  // namespace
 
-int32_t solve_chunk_target(int32_t n) {
+// Large systems: two grid lines per chunk, which measured fastest on 96-,
+// 128- and 160-wide grids (one line per chunk doubles the hand-offs between
+// chunks through global memory; three lines lengthen each chunk's chain and
+// leave fewer chunks in flight).  The chunk cut then goes to the line start
+// nearest the target.
+int32_t auto_solve_chunk_target(const bilu_pattern* p) {
+  const long long t = (long long)p->n / (10LL * device_sm_count());
+  if (t >= 256 && p->line_len >= 16 && p->line_len <= 192) return 2 * p->line_len;
+  return (int32_t)std::max(32LL, std::min(256LL, t));
+}
+
+int32_t solve_chunk_target(const bilu_pattern* p) {
   const int c = trisolve_config().chunk;
-  if (c > 0) return c;
-  const long long t = (long long)n / (10LL * device_sm_count());
-  return (int32_t)std::max(32LL, std::min(200LL, t));
+  return c > 0 ? c : auto_solve_chunk_target(p);
 }
 
 int32_t factor_chunk_target(int32_t n) {

@@ -172,3 +172,23 @@ def test_chunks_without_line_structure_use_the_target(libbilu):
     P = B.bilu_symbolic(n, rp, ci, 0)
     bnd = P.schedule(64)["bounds"]
     assert bnd.tolist() == list(range(0, n, 64)) + [n]
+
+
+@pytest.mark.parametrize("dims,stencil,k,want,chunk", [
+    ((96, 96, 48), 7, 1, 192, 192),     # two 96-row grid lines
+    ((128, 128, 24), 7, 1, 256, 256),   # two 128-row grid lines
+    ((160, 160, 16), 27, 0, 320, 320),  # two 160-row grid lines of a 27-point grid
+    ((300, 300, 5), 7, 0, 256, 300),    # lines longer than 192 rows: the size rule's cap,
+])                                      # cut at the nearest line start
+def test_auto_chunk_target_is_two_grid_lines(libbilu, dims, stencil, k, want, chunk):
+    """Large systems (n / (10 * SMs) >= 256 rows, on any part with up to 152
+    SMs) get two grid lines per chunk: the pattern's line length is the most
+    common distance between rows that do not depend on their predecessor."""
+    import paper_1703_01325_gb300.bilu as B
+    from paper_1703_01325_gb300.reservoir import reservoir_system
+    S = reservoir_system(*dims, 1, stencil=stencil, sigma=1.0, accum=0.01)
+    P = B.bilu_symbolic(S.n, S.row_ptr, S.col_idx, k)
+    assert B.bilu_auto_trisolve_chunk(P) == want
+    # and the schedule cut at that target holds whole lines (plane ends aside)
+    lens = np.diff(P.schedule(want)["bounds"])
+    assert np.bincount(lens).argmax() == chunk
