@@ -34,7 +34,9 @@ int32_t bilu_get_trisolve_chunk(void);
 int32_t bilu_auto_trisolve_chunk(const bilu_pattern* p);
 
 /* Target of consecutive block rows one CTA owns in the sync-free
- * factorization: 0 (the default) picks n / (2 * SMs) clamped to [64, 256];
+ * factorization: 0 (the default) picks n / (2 * SMs) clamped to [64, 256],
+ * or 3 L (three grid lines) where that hits 256 and a line length L of
+ * 16..128 rows is detected (see bilu_set_trisolve_chunk);
  * 1 <= rows <= 1024 fixes it; other values: BILU_ERR_ARG.  Its schedule is
  * separate from the solves' and is rebuilt by the next factorization. */
 int bilu_set_factor_chunk(int32_t rows);

@@ -21,7 +21,7 @@ int solve_schedule(const bilu_pattern* p) {
   return ensure_schedule(p, &const_cast<bilu_pattern*>(p)->solve, solve_chunk_target(p), true);
 }
 int factor_schedule(const bilu_pattern* p) {
-  return ensure_schedule(p, &const_cast<bilu_pattern*>(p)->fact, factor_chunk_target(p->n), false);
+  return ensure_schedule(p, &const_cast<bilu_pattern*>(p)->fact, factor_chunk_target(p), false);
 }
 
 int ready(const bilu_pattern* p) {
@@ -102,7 +102,7 @@ extern "C" int bilu_pattern_upload(bilu_pattern* p, void* stream) {
   p->d_mem = mem;
   p->device = dev;
   if (ensure_schedule(p, &p->solve, solve_chunk_target(p), true) != 0 ||
-      (!p->is_transpose && ensure_schedule(p, &p->fact, factor_chunk_target(p->n), false) != 0))
+      (!p->is_transpose && ensure_schedule(p, &p->fact, factor_chunk_target(p), false) != 0))
     return BILU_ERR_OOM;
   return BILU_OK;
 }

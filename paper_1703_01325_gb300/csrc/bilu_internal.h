@@ -99,14 +99,14 @@ struct TrisolveConfig {
   int skip_row = -1;       // test hook: this row of the lower solve is never published
 };
 TrisolveConfig& trisolve_config();
-// The chunk targets in effect for a system of n block rows: the configured
-// ones, or (0) n / (10 * SMs) in [32, 256] for the solves -- two grid lines
-// instead where that rule hits its cap and a line length of 16..192 rows is
-// detected -- and n / (2 * SMs) in
-// [64, 256] for the factorization -- enough chunks to fill the GPU.
+// The chunk targets in effect for a pattern of n block rows: the configured
+// ones, or (0) n / (10 * SMs) in [32, 256] for the solves and n / (2 * SMs)
+// in [64, 256] for the factorization -- enough chunks to fill the GPU --
+// except on large grids with a detected line length L: 2 L for the solves
+// (16 <= L <= 192), 3 L for the factorization (16 <= L <= 128).
 int32_t solve_chunk_target(const bilu_pattern* p);
 int32_t auto_solve_chunk_target(const bilu_pattern* p);  // the rule alone
-int32_t factor_chunk_target(int32_t n);
+int32_t factor_chunk_target(const bilu_pattern* p);
 
 // Brackets one kernel launch with profiling events (when enabled) and counts it.
 class ProfScope {
