@@ -42,6 +42,10 @@ int32_t bilu_auto_trisolve_chunk(const bilu_pattern* p);
 int bilu_set_factor_chunk(int32_t rows);
 int32_t bilu_get_factor_chunk(void);
 
+/* The target the factorization uses for pattern p when none is set, for
+ * inspection (as bilu_auto_trisolve_chunk).  Returns -1 for a NULL p. */
+int32_t bilu_auto_factor_chunk(const bilu_pattern* p);
+
 /* Warps per CTA in the triangular solves: 4 (default), 8 or 16, else
  * BILU_ERR_ARG.  More warps per chunk give each row more time to fetch its
  * operands ahead of its dependencies. */

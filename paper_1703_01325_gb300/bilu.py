@@ -408,6 +408,11 @@ def bilu_auto_trisolve_chunk(P: "Pattern") -> int:
     return int(L.load().bilu_auto_trisolve_chunk(P.handle))
 
 
+def bilu_auto_factor_chunk(P: "Pattern") -> int:
+    """The chunk target the factorization uses for P when none is set."""
+    return int(L.load().bilu_auto_factor_chunk(P.handle))
+
+
 def bilu_set_factor_chunk(rows: int):
     _check(L.load().bilu_set_factor_chunk(rows), "bilu_set_factor_chunk")
 

@@ -400,6 +400,10 @@ extern "C" int32_t bilu_auto_trisolve_chunk(const bilu_pattern* p) {
   return p ? auto_solve_chunk_target(p) : -1;
 }
 
+extern "C" int32_t bilu_auto_factor_chunk(const bilu_pattern* p) {
+  return p ? auto_factor_chunk_target(p) : -1;
+}
+
 extern "C" int bilu_set_trisolve_warps(int32_t warps) {
   if (warps != 4 && warps != 8 && warps != 16) return BILU_ERR_ARG;
   trisolve_config().warps = warps;

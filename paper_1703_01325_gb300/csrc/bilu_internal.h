@@ -107,6 +107,7 @@ TrisolveConfig& trisolve_config();
 int32_t solve_chunk_target(const bilu_pattern* p);
 int32_t auto_solve_chunk_target(const bilu_pattern* p);  // the rule alone
 int32_t factor_chunk_target(const bilu_pattern* p);
+int32_t auto_factor_chunk_target(const bilu_pattern* p);  // the rule alone
 
 // Brackets one kernel launch with profiling events (when enabled) and counts it.
 class ProfScope {

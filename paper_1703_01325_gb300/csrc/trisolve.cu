@@ -88,12 +88,15 @@ int32_t solve_chunk_target(const bilu_pattern* p) {
 
 // The factorization's 8-warp CTAs do best with three grid lines per chunk on
 // large grids (128-wide: 12.4 ms against 13.7 with two lines).
-int32_t factor_chunk_target(const bilu_pattern* p) {
-  const int c = trisolve_config().factor_chunk;
-  if (c > 0) return c;
+int32_t auto_factor_chunk_target(const bilu_pattern* p) {
   const long long t = (long long)p->n / (2LL * device_sm_count());
   if (t >= 256 && p->line_len >= 16 && p->line_len <= 128) return 3 * p->line_len;
   return (int32_t)std::max(64LL, std::min(256LL, t));
+}
+
+int32_t factor_chunk_target(const bilu_pattern* p) {
+  const int c = trisolve_config().factor_chunk;
+  return c > 0 ? c : auto_factor_chunk_target(p);
 }
 
 namespace {

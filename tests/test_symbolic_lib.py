@@ -174,6 +174,21 @@ def test_chunks_without_line_structure_use_the_target(libbilu):
     assert bnd.tolist() == list(range(0, n, 64)) + [n]
 
 
+@pytest.mark.parametrize("dims,stencil,k,want", [
+    ((96, 96, 48), 7, 1, 288),     # three 96-row grid lines
+    ((128, 128, 24), 7, 1, 384),   # three 128-row grid lines
+    ((160, 160, 16), 27, 0, 256),  # lines longer than 128 rows: the size rule's cap
+])
+def test_auto_factor_chunk_target_is_three_grid_lines(libbilu, dims, stencil, k, want):
+    """Large systems (n / (2 * SMs) >= 256 rows) factor in chunks of three grid
+    lines, from the same line length as the solves' chunks."""
+    import paper_1703_01325_gb300.bilu as B
+    from paper_1703_01325_gb300.reservoir import reservoir_system
+    S = reservoir_system(*dims, 1, stencil=stencil, sigma=1.0, accum=0.01)
+    P = B.bilu_symbolic(S.n, S.row_ptr, S.col_idx, k)
+    assert B.bilu_auto_factor_chunk(P) == want
+
+
 @pytest.mark.parametrize("dims,stencil,k,want,chunk", [
     ((96, 96, 48), 7, 1, 192, 192),     # two 96-row grid lines
     ((128, 128, 24), 7, 1, 256, 256),   # two 128-row grid lines
