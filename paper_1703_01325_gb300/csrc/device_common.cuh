@@ -25,6 +25,25 @@ __device__ __forceinline__ unsigned long long ld_relaxed_u64(const void* p) {
 __device__ __forceinline__ void st_relaxed_u64(void* p, unsigned long long v) {
   asm volatile("st.relaxed.gpu.global.b64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
+__device__ __forceinline__ unsigned ld_relaxed_u32(const void* p) {
+  unsigned v;
+  asm volatile("ld.relaxed.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_relaxed_u32(void* p, unsigned v) {
+  asm volatile("st.relaxed.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+// Relaxed load / store of a value's bit pattern (32 or 64 bits).
+template <typename U>
+__device__ __forceinline__ U ld_relaxed_bits(const void* p) {
+  if constexpr (sizeof(U) == 8) return ld_relaxed_u64(p);
+  else return ld_relaxed_u32(p);
+}
+template <typename U>
+__device__ __forceinline__ void st_relaxed_bits(void* p, U v) {
+  if constexpr (sizeof(U) == 8) st_relaxed_u64(p, v);
+  else st_relaxed_u32(p, v);
+}
 __device__ __forceinline__ int ld_acquire_s32(const int* p) {
   int v;
   asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
@@ -40,13 +59,6 @@ __device__ __forceinline__ long long global_ns() {
   unsigned long long t;
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
   return (long long)t;
-}
-
-// Publish one computed value for the sync-free solves.
-__device__ __forceinline__ void publish(double* p, double v) {
-  unsigned long long u = (unsigned long long)__double_as_longlong(v);
-  if (u == kPending) u = kQuietNaN;
-  st_relaxed_u64(p, u);
 }
 
 // Bounded wait state: the first waiter that runs out of time records
@@ -72,41 +84,6 @@ struct Waiter {
   }
 };
 
-// Wait until *p holds a computed value; false if the wait was abandoned.
-__device__ __forceinline__ bool wait_value(const double* p, double& out, Waiter& w) {
-  w.t0 = 0;  // the time limit applies to each wait separately
-  for (unsigned it = 1;; ++it) {
-    unsigned long long u = ld_relaxed_u64(p);
-    if (u != kPending) {
-      out = __longlong_as_double((long long)u);
-      return true;
-    }
-    if (w.give_up(it)) return false;
-  }
-}
-
-// Wait until all N values at p hold computed values (each polled with a
-// relaxed load; the N loads of a round are issued together, so a dependency
-// costs one L2 round trip rather than N); false if the wait was abandoned.
-template <int N>
-__device__ __forceinline__ bool wait_values(const double* p, double (&out)[N], Waiter& w) {
-  w.t0 = 0;
-  for (unsigned it = 1;; ++it) {
-    unsigned long long u[N];
-#pragma unroll
-    for (int q = 0; q < N; ++q) u[q] = ld_relaxed_u64(p + q);
-    bool all = true;
-#pragma unroll
-    for (int q = 0; q < N; ++q) all = all && (u[q] != kPending);
-    if (all) {
-#pragma unroll
-      for (int q = 0; q < N; ++q) out[q] = __longlong_as_double((long long)u[q]);
-      return true;
-    }
-    if (w.give_up(it)) return false;
-  }
-}
-
 // Bit patterns of a value type for the shared-memory value cache of the
 // solves: "pending" is a signalling NaN with a fixed payload (no arithmetic
 // produces one), "quiet" replaces a computed value that would collide.
@@ -126,6 +103,41 @@ struct ValueBits<float> {
   __device__ static U bits(float v) { return (U)__float_as_uint(v); }
   __device__ static float value(U u) { return __uint_as_float(u); }
 };
+
+// Publish one computed value of type TV for the sync-free solves: its bit
+// pattern, relaxed (the value is its own ready flag); a value that would
+// carry the pending pattern is stored as a quiet NaN.
+template <typename TV>
+__device__ __forceinline__ void publish_value(TV* p, TV v) {
+  using VB = ValueBits<TV>;
+  typename VB::U u = VB::bits(v);
+  if (u == VB::kPend) u = VB::kQuiet;
+  st_relaxed_bits<typename VB::U>(p, u);
+}
+
+// Wait until all N values of type TV in global memory at p hold computed
+// values (relaxed loads, issued together each round: one L2 round trip per
+// poll); false if the wait was abandoned.
+template <int N, typename TV>
+__device__ __forceinline__ bool wait_values_global(const TV* p, TV (&out)[N], Waiter& w) {
+  using VB = ValueBits<TV>;
+  using U = typename VB::U;
+  w.t0 = 0;
+  for (unsigned it = 1;; ++it) {
+    U u[N];
+#pragma unroll
+    for (int q = 0; q < N; ++q) u[q] = ld_relaxed_bits<U>(p + q);
+    bool all = true;
+#pragma unroll
+    for (int q = 0; q < N; ++q) all = all && (u[q] != VB::kPend);
+    if (all) {
+#pragma unroll
+      for (int q = 0; q < N; ++q) out[q] = VB::value(u[q]);
+      return true;
+    }
+    if (w.give_up(it)) return false;
+  }
+}
 
 // Wait until all N values of type TV in this CTA's shared memory at p hold
 // computed values (volatile loads: each value is its own ready flag, so no

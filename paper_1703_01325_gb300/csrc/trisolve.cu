@@ -43,8 +43,11 @@
 // widest row in one pass (at least a quarter of the 32 / B lanes' groups).
 //
 // TV is the type the factors are stored and applied in: double, or float for
-// the mixed-precision solver (vectors stay double; each value read is
-// converted, the arithmetic runs in TV).
+// the mixed-precision solver.  The sweeps' own vectors (y, z and the upper
+// sweep's x) are kept in TV in the workspace, so an FP32 sweep converts
+// nothing on its chain of dependent rows (a double <-> float conversion runs
+// at the FP64 rate on this part); only r is read in double, and a last pass
+// widens x to the caller's double vector.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -102,14 +105,16 @@ int32_t factor_chunk_target(const bilu_pattern* p) {
 namespace {
 
 
-__global__ void apply_prep_kernel(double* y, double* x, long long m, int32_t* header, const int32_t* stop) {
+template <typename TV>
+__global__ void apply_prep_kernel(TV* y, TV* x, long long m, int32_t* header, const int32_t* stop) {
   // Each apply starts with a clean header: its status is its own.  Both
-  // solves' outputs start "pending".
+  // sweeps' outputs start "pending".
+  using VB = ValueBits<TV>;
   if (stop && *stop) return;
   const long long stride = (long long)gridDim.x * blockDim.x;
   for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < m; q += stride) {
-    reinterpret_cast<unsigned long long*>(y)[q] = kPending;
-    reinterpret_cast<unsigned long long*>(x)[q] = kPending;
+    reinterpret_cast<typename VB::U*>(y)[q] = VB::kPend;
+    reinterpret_cast<typename VB::U*>(x)[q] = VB::kPend;
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     header[kTicketL] = 0;
@@ -120,23 +125,23 @@ __global__ void apply_prep_kernel(double* y, double* x, long long m, int32_t* he
 }
 
 // Registers a lane holds for one row: the row, its first block of this lane's
-// group (column, this lane's B values, optimistic dependency values), and the
-// row's own term (r_i for L, z_i for U').
-template <int B, typename TV>
+// group (column, this lane's B values, optimistic dependency values, as bit
+// patterns of TV), and the row's own term (r_i for L, z_i for U', type RT).
+template <int B, typename TV, typename RT>
 struct RowPre {
   int i, beg, end, j;
   TV av[B];
-  unsigned long long yv[B];  // dependency values of a block outside the chunk, read early
-  double own;                // lanes < B: r_i[lane] or z_i[lane]
+  typename ValueBits<TV>::U yv[B];  // dependency values of a block outside the chunk, read early
+  RT own;                           // lanes < B: r_i[lane] or z_i[lane]
 };
 
 // Stage A of the prefetch: the row, its first block (column and values) and
 // its own term.
-template <int B, typename TV>
-__device__ __forceinline__ void fetch_row(RowPre<B, TV>& p, int pos, int len, const int* s_i,
+template <int B, typename TV, typename RT>
+__device__ __forceinline__ void fetch_row(RowPre<B, TV, RT>& p, int pos, int len, const int* s_i,
                                           const int* s_beg, const int* s_end,
                                           const int32_t* __restrict__ ci, const TV* __restrict__ vals,
-                                          const double* rhs, int g, int rr, bool act, int lane) {
+                                          const RT* rhs, int g, int rr, bool act, int lane) {
   if (pos >= len) {  // past the chunk's end: nothing to fetch, no dependency to read
     p.i = -1;
     p.beg = p.end = 0;
@@ -159,18 +164,20 @@ __device__ __forceinline__ void fetch_row(RowPre<B, TV>& p, int pos, int len, co
 
 // Stage B: a dependency outside the chunk is usually final already: read it
 // now (relaxed); if it still holds the pending pattern it is waited for later.
-template <int B, typename TV>
-__device__ __forceinline__ void fetch_deps(RowPre<B, TV>& p, const double* out, int lo, int hi) {
+template <int B, typename TV, typename RT>
+__device__ __forceinline__ void fetch_deps(RowPre<B, TV, RT>& p, const TV* out, int lo, int hi) {
+  using VB = ValueBits<TV>;
   const bool remote = p.j >= 0 && (p.j < lo || p.j >= hi);
 #pragma unroll
-  for (int q = 0; q < B; ++q) p.yv[q] = remote ? ld_relaxed_u64(out + (size_t)p.j * B + q) : kPending;
+  for (int q = 0; q < B; ++q)
+    p.yv[q] = remote ? ld_relaxed_bits<typename VB::U>(out + (size_t)p.j * B + q) : VB::kPend;
 }
 
 // z = D^{-1} y in place: R = 32 / B block rows per warp, lane (row, r) forms
 // z[row][r] = sum_c D^{-1}[r][c] y[row][c] (blocks column-major).  A row's
 // lanes sit in one warp; they read all of y_row before any of them writes.
 template <int B, typename TV>
-__global__ void __launch_bounds__(256) diag_scale_kernel(int32_t n, const TV* __restrict__ dinv, double* y,
+__global__ void __launch_bounds__(256) diag_scale_kernel(int32_t n, const TV* __restrict__ dinv, TV* y,
                                                          const int32_t* stop) {
   constexpr int R = 32 / B;
   if (stop && ld_volatile_s32(stop)) return;
@@ -183,26 +190,31 @@ __global__ void __launch_bounds__(256) diag_scale_kernel(int32_t n, const TV* __
   TV z = TV(0);
   if (act) {
     const TV* d = dinv + (size_t)row * (B * B) + r;
-    const double* yr = y + (size_t)row * B;
+    const TV* yr = y + (size_t)row * B;
 #pragma unroll
-    for (int c = 0; c < B; ++c) {
-      TV yc;
-      if constexpr (sizeof(TV) == 4) yc = d2f_rn(yr[c]);
-      else yc = yr[c];
-      z = fma(__ldg(d + c * B), yc, z);
-    }
+    for (int c = 0; c < B; ++c) z = fma(__ldg(d + c * B), yr[c], z);
   }
   __syncwarp();
-  if (act) y[(size_t)row * B + r] = (double)z;
+  if (act) y[(size_t)row * B + r] = z;
+}
+
+// x = (double) x32 over the FP32 apply's result.
+__global__ void __launch_bounds__(256) widen_kernel(const float* __restrict__ src, double* __restrict__ dst,
+                                                    long long m, const int32_t* stop) {
+  if (stop && ld_volatile_s32(stop)) return;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < m; q += stride)
+    dst[q] = (double)src[q];
 }
 
 // GE: the groups a row's blocks are spread over (a power of two, at most
-// groups_for(B)); the partial sums take log2(GE) reduction steps.
-template <int B, bool UPPER, typename TV, int kTriWarps, int GE>
+// groups_for(B)); the partial sums take log2(GE) reduction steps.  RT: the
+// type of the right-hand side (double r for L, TV z for U').
+template <int B, bool UPPER, typename TV, int kTriWarps, int GE, typename RT>
 __global__ void __launch_bounds__(kTriWarps * 32) tri_solve_kernel(
     int32_t n, int32_t chunk, int32_t nchunks, const int32_t* __restrict__ bnd, const int32_t* __restrict__ rp,
     const int32_t* __restrict__ ci, const TV* __restrict__ vals,
-    const int32_t* __restrict__ ord, const int32_t* __restrict__ tick, const double* rhs, double* out,
+    const int32_t* __restrict__ ord, const int32_t* __restrict__ tick, const RT* rhs, TV* out,
     int32_t* header, long long spin_ns, int32_t skip_row, int32_t* stop) {
   static_assert(GE >= 1 && GE <= groups_for(B) && (GE & (GE - 1)) == 0, "group count");
   constexpr int G = GE;
@@ -241,13 +253,13 @@ __global__ void __launch_bounds__(kTriWarps * 32) tri_solve_kernel(
     }
     for (int q = tid; q < len * B; q += blockDim.x) reinterpret_cast<typename VB::U*>(yl)[q] = VB::kPend;
     __syncthreads();
-    RowPre<B, TV> cur, nx1, nx2;
-    fetch_row<B, TV>(cur, warp, len, s_i, s_beg, s_end, ci, vals, rhs, g, rr, act, lane);
-    fetch_deps<B, TV>(cur, out, lo, hi);
-    fetch_row<B, TV>(nx1, warp + kTriWarps, len, s_i, s_beg, s_end, ci, vals, rhs, g, rr, act, lane);
+    RowPre<B, TV, RT> cur, nx1, nx2;
+    fetch_row<B, TV, RT>(cur, warp, len, s_i, s_beg, s_end, ci, vals, rhs, g, rr, act, lane);
+    fetch_deps<B, TV, RT>(cur, out, lo, hi);
+    fetch_row<B, TV, RT>(nx1, warp + kTriWarps, len, s_i, s_beg, s_end, ci, vals, rhs, g, rr, act, lane);
     for (int pos = warp; pos < len && !dead; pos += kTriWarps) {
-      fetch_row<B, TV>(nx2, pos + 2 * kTriWarps, len, s_i, s_beg, s_end, ci, vals, rhs, g, rr, act, lane);
-      fetch_deps<B, TV>(nx1, out, lo, hi);
+      fetch_row<B, TV, RT>(nx2, pos + 2 * kTriWarps, len, s_i, s_beg, s_end, ci, vals, rhs, g, rr, act, lane);
+      fetch_deps<B, TV, RT>(nx1, out, lo, hi);
       const int i = cur.i;
       bool ok = true;
       // The row's own term (r_i or z_i) seeds the sum of group 0 (lanes < B);
@@ -259,7 +271,7 @@ __global__ void __launch_bounds__(kTriWarps * 32) tri_solve_kernel(
         if (act && t < cur.end) {
           int j;
           TV av[B];
-          unsigned long long yv[B];
+          typename VB::U yv[B];
           if (t0 == cur.beg) {
             j = cur.j;
 #pragma unroll
@@ -273,23 +285,20 @@ __global__ void __launch_bounds__(kTriWarps * 32) tri_solve_kernel(
 #pragma unroll
             for (int q = 0; q < B; ++q) {
               av[q] = __ldg(a + q * B);
-              yv[q] = kPending;
+              yv[q] = VB::kPend;
             }
           }
           TV yt[B];
           if (j >= lo && j < hi) {
             ok = wait_values_shared<B, TV>(yl + (size_t)(j - lo) * B, yt, w);
           } else {
-            double yj[B];
             bool have = true;
 #pragma unroll
             for (int q = 0; q < B; ++q) {
-              have = have && (yv[q] != kPending);
-              yj[q] = __longlong_as_double((long long)yv[q]);
+              have = have && (yv[q] != VB::kPend);
+              yt[q] = VB::value(yv[q]);
             }
-            if (!have) ok = wait_values<B>(out + (size_t)j * B, yj, w);
-#pragma unroll
-            for (int q = 0; q < B; ++q) yt[q] = (TV)yj[q];
+            if (!have) ok = wait_values_global<B, TV>(out + (size_t)j * B, yt, w);
           }
           if (ok) {
 #pragma unroll
@@ -309,7 +318,7 @@ __global__ void __launch_bounds__(kTriWarps * 32) tri_solve_kernel(
         typename VB::U u = VB::bits(vt);
         if (u == VB::kPend) u = VB::kQuiet;
         reinterpret_cast<volatile typename VB::U*>(yl)[(size_t)(i - lo) * B + lane] = u;
-        if (i != skip_row) publish(out + (size_t)i * B + lane, (double)vt);
+        if (i != skip_row) publish_value<TV>(out + (size_t)i * B + lane, vt);
       }
       cur = nx1;
       nx1 = nx2;
@@ -336,15 +345,15 @@ size_t tri_smem_bytes(int chunk, int b) {
 // Persistent grid: as many CTAs as fit on the device at once (cached per
 // shared-memory size; the occupancy query is host work worth skipping per
 // launch).
-template <int B, bool UPPER, typename TV, int kTriWarps, int GE>
+template <int B, bool UPPER, typename TV, int kTriWarps, int GE, typename RT>
 int tri_grid(size_t smem, int nchunks) {
   static size_t last_smem = 0;
   static int last_per_sm = 1;
   if (smem != last_smem) {
-    cudaFuncSetAttribute(tri_solve_kernel<B, UPPER, TV, kTriWarps, GE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)std::max<size_t>(smem, 48 * 1024));
+    cudaFuncSetAttribute(tri_solve_kernel<B, UPPER, TV, kTriWarps, GE, RT>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)std::max<size_t>(smem, 48 * 1024));
     int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tri_solve_kernel<B, UPPER, TV, kTriWarps, GE>,
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tri_solve_kernel<B, UPPER, TV, kTriWarps, GE, RT>,
                                                   kTriWarps * 32, smem);
     last_per_sm = per_sm < 1 ? 1 : per_sm;
     last_smem = smem;
@@ -352,55 +361,57 @@ int tri_grid(size_t smem, int nchunks) {
   return std::max(1, std::min(nchunks, last_per_sm * sm_count()));
 }
 
-// One triangular solve (the arguments of tri_solve_kernel).
-template <typename TV>
+// One triangular sweep (the arguments of tri_solve_kernel).
+template <typename TV, typename RT>
 struct TriArgs {
   int32_t n, chunk, nchunks;
   const int32_t *bnd, *rp, *ci;
   const TV* vals;
   const int32_t *ord, *tick;
-  const double* rhs;
-  double* out;
+  const RT* rhs;
+  TV* out;
   int32_t* header;
   long long spin_ns;
   int32_t skip_row;
   int32_t* stop;
 };
 
-template <int B, bool UPPER, typename TV, int W, int GE>
-void launch_tri(const TriArgs<TV>& a, size_t smem, cudaStream_t s) {
-  const int grid = tri_grid<B, UPPER, TV, W, GE>(smem, a.nchunks);
-  tri_solve_kernel<B, UPPER, TV, W, GE><<<grid, W * 32, smem, s>>>(a.n, a.chunk, a.nchunks, a.bnd, a.rp, a.ci, a.vals,
-                                                                  a.ord, a.tick, a.rhs, a.out, a.header,
-                                                                  a.spin_ns, a.skip_row, a.stop);
+template <int B, bool UPPER, typename TV, int W, int GE, typename RT>
+void launch_tri(const TriArgs<TV, RT>& a, size_t smem, cudaStream_t s) {
+  const int grid = tri_grid<B, UPPER, TV, W, GE, RT>(smem, a.nchunks);
+  tri_solve_kernel<B, UPPER, TV, W, GE, RT><<<grid, W * 32, smem, s>>>(
+      a.n, a.chunk, a.nchunks, a.bnd, a.rp, a.ci, a.vals, a.ord, a.tick, a.rhs, a.out, a.header, a.spin_ns,
+      a.skip_row, a.stop);
 }
 
 // The fewest groups (a power of two, at least groups_for(B) / 4) that hold
 // every row's blocks in one pass: narrow rows (ILU(0) of a 7-point stencil:
 // 3 blocks) then take fewer reduction steps.  Only the default 4-warp CTA has
 // the narrower instantiations.
-template <int B, bool UPPER, typename TV, int W>
-void launch_tri_groups(const TriArgs<TV>& a, int32_t max_blocks, size_t smem, cudaStream_t s) {
+template <int B, bool UPPER, typename TV, int W, typename RT>
+void launch_tri_groups(const TriArgs<TV, RT>& a, int32_t max_blocks, size_t smem, cudaStream_t s) {
   constexpr int G = groups_for(B);
   const int32_t need = max_blocks;
   if constexpr (W == 4) {
-    if (need <= G / 4) return launch_tri<B, UPPER, TV, W, G / 4>(a, smem, s);
-    if (need <= G / 2) return launch_tri<B, UPPER, TV, W, G / 2>(a, smem, s);
+    if (need <= G / 4) return launch_tri<B, UPPER, TV, W, G / 4, RT>(a, smem, s);
+    if (need <= G / 2) return launch_tri<B, UPPER, TV, W, G / 2, RT>(a, smem, s);
   }
-  launch_tri<B, UPPER, TV, W, G>(a, smem, s);
+  launch_tri<B, UPPER, TV, W, G, RT>(a, smem, s);
 }
 
+// L y = r (y in TV), z = D^{-1} y in place, U' x = z (x in TV: the caller's
+// vector in FP64, a workspace vector widened afterwards in FP32).
 template <int B, typename TV, int W>
 void launch_solves(const bilu_pattern* p, int chunk, int nchunks, const TV* L, const TV* Dinv,
-                   const TV* U, const double* r, double* y, double* x, int32_t* header, const TrisolveConfig& cfg,
+                   const TV* U, const double* r, TV* y, TV* x, int32_t* header, const TrisolveConfig& cfg,
                    int32_t* stop, void* stream) {
   cudaStream_t s = (cudaStream_t)stream;
   const size_t smem = tri_smem_bytes<TV>(chunk, B);
   {
-    const TriArgs<TV> a{p->n, chunk, nchunks, p->solve.d_bnd, p->d_lrp, p->d_lci, L,
-                        p->solve.d_ord_l, p->solve.d_tick_l, r, y, header, cfg.spin_ns, cfg.skip_row, stop};
+    const TriArgs<TV, double> a{p->n, chunk, nchunks, p->solve.d_bnd, p->d_lrp, p->d_lci, L,
+                                p->solve.d_ord_l, p->solve.d_tick_l, r, y, header, cfg.spin_ns, cfg.skip_row, stop};
     ProfScope ps(BILU_PROF_LOWER, stream);
-    launch_tri_groups<B, false, TV, W>(a, p->max_l, smem, s);
+    launch_tri_groups<B, false, TV, W, double>(a, p->max_l, smem, s);
   }
   {
     // z = D^{-1} y over y.  A lower sweep that gave up (a bounded wait ran
@@ -412,10 +423,10 @@ void launch_solves(const bilu_pattern* p, int chunk, int nchunks, const TV* L, c
     diag_scale_kernel<B, TV><<<(unsigned)blocks, 256, 0, s>>>(p->n, Dinv, y, stop);
   }
   {
-    const TriArgs<TV> a{p->n, chunk, nchunks, p->solve.d_bnd, p->d_urp, p->d_uci, U,
-                        p->solve.d_ord_u, p->solve.d_tick_u, y, x, header, cfg.spin_ns, -1, stop};
+    const TriArgs<TV, TV> a{p->n, chunk, nchunks, p->solve.d_bnd, p->d_urp, p->d_uci, U,
+                            p->solve.d_ord_u, p->solve.d_tick_u, y, x, header, cfg.spin_ns, -1, stop};
     ProfScope ps(BILU_PROF_UPPER, stream);
-    launch_tri_groups<B, true, TV, W>(a, p->max_u, smem, s);
+    launch_tri_groups<B, true, TV, W, TV>(a, p->max_u, smem, s);
   }
 }
 
@@ -430,25 +441,34 @@ int launch_apply_t(const bilu_pattern* p, int32_t b, const TV* f, const double* 
   const int chunk = p->solve.max_len;  // shared-memory rows per CTA
   const int nchunks = p->solve.nchunks;
   int32_t* header = reinterpret_cast<int32_t*>(work);
-  double* y = reinterpret_cast<double*>(reinterpret_cast<char*>(work) + kHeaderBytes);
+  const long long m = (long long)n * b;
+  // The workspace's vector region holds n*b doubles: y (FP64), or y and the
+  // upper sweep's x side by side (FP32).
+  TV* y = reinterpret_cast<TV*>(reinterpret_cast<char*>(work) + kHeaderBytes);
+  TV* xs;
+  if constexpr (sizeof(TV) == 8) xs = reinterpret_cast<TV*>(x);
+  else xs = y + m;
   const size_t bb = (size_t)b * b;
   const TV* L = f;
   const TV* Dinv = f + (size_t)p->nnz_l() * bb;
   const TV* U = Dinv + (size_t)n * bb;
-  const long long m = (long long)n * b;
   const int prep_blocks = (int)std::min<long long>((m + 255) / 256, (long long)sm_count() * 8);
   {
     ProfScope ps(BILU_PROF_APPLY_PREP, stream);
-    apply_prep_kernel<<<prep_blocks, 256, 0, s>>>(y, x, m, header, stop);
+    apply_prep_kernel<TV><<<prep_blocks, 256, 0, s>>>(y, xs, m, header, stop);
   }
   BILU_DISPATCH_B(b, {
     if (cfg.warps == 16)
-      launch_solves<B, TV, 16>(p, chunk, nchunks, L, Dinv, U, r, y, x, header, cfg, stop, stream);
+      launch_solves<B, TV, 16>(p, chunk, nchunks, L, Dinv, U, r, y, xs, header, cfg, stop, stream);
     else if (cfg.warps == 4)
-      launch_solves<B, TV, 4>(p, chunk, nchunks, L, Dinv, U, r, y, x, header, cfg, stop, stream);
+      launch_solves<B, TV, 4>(p, chunk, nchunks, L, Dinv, U, r, y, xs, header, cfg, stop, stream);
     else
-      launch_solves<B, TV, 8>(p, chunk, nchunks, L, Dinv, U, r, y, x, header, cfg, stop, stream);
+      launch_solves<B, TV, 8>(p, chunk, nchunks, L, Dinv, U, r, y, xs, header, cfg, stop, stream);
   });
+  if constexpr (sizeof(TV) == 4) {
+    ProfScope ps(BILU_PROF_APPLY_PREP, stream);
+    widen_kernel<<<prep_blocks, 256, 0, s>>>(xs, x, m, stop);
+  }
   return (int)cudaGetLastError();
 }
 
