@@ -207,3 +207,17 @@ def test_auto_chunk_target_is_two_grid_lines(libbilu, dims, stencil, k, want, ch
     # and the schedule cut at that target holds whole lines (plane ends aside)
     lens = np.diff(P.schedule(want)["bounds"])
     assert np.bincount(lens).argmax() == chunk
+
+
+@pytest.mark.parametrize("n,seed", [(3000, 1), (20000, 2)])
+def test_auto_chunk_targets_without_grid_lines(libbilu, n, seed):
+    """A pattern without recurring line starts falls back to the size rules:
+    n / (10 * SMs) in [32, 256] for the solves, n / (2 * SMs) in [64, 256]
+    for the factorization (SMs = 1 when the library sees no GPU)."""
+    import paper_1703_01325_gb300.bilu as B
+    torch = pytest.importorskip("torch")
+    sms = torch.cuda.get_device_properties(0).multi_processor_count if torch.cuda.is_available() else 1
+    rp, ci = random_pattern(n, density=4.0 / n, seed=seed)
+    P = B.bilu_symbolic(n, rp, ci, 0)
+    assert B.bilu_auto_trisolve_chunk(P) == max(32, min(256, n // (10 * sms)))
+    assert B.bilu_auto_factor_chunk(P) == max(64, min(256, n // (2 * sms)))
