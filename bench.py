@@ -43,8 +43,8 @@ METRIC = "Block-ILU(k) BiCGSTAB ms to 1e-8 resid; trisolve/SpMV GB/s; FP32-prec 
 WORKLOAD = "grid128x128x64_7pt_b3"
 FP64_PEAK_TFLOPS = 1.196  # measured FP64 FMA rate of this GB300 (FMA = 2 flops)
 # DRAM bytes (read + write) per launch of a kernel, from one ncu capture of the
-# kernel as it stands (profiles/trisolve_spmv_factor_grid96x96x48_b3_k1.md holds
-# the summary and the command); keyed by (workload, k, kernel).  The capture
+# kernel as it stands (the summary under profiles/ gives the command); keyed by
+# (workload, k, kernel).  The capture
 # runs on the 96 x 96 x 48 case (the recipe's size rule); a solve streams each
 # factor block once, so its traffic is scaled to the 128 x 128 x 64 launch by
 # the algorithmic bytes.  Missing entries (no capture of the kernel as it

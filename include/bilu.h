@@ -22,8 +22,12 @@
  *    call is stream ordered and returns once its work is enqueued unless the
  *    call says it synchronises.
  *  - The caller owns every device buffer passed in (vectors, values, factor
- *    buffer, workspace).  The library allocates device memory only in
- *    bilu_pattern_upload (set-up), never in factor, apply, SpMV or solve.
+ *    buffer, workspace).  The library allocates device memory only in the
+ *    set-up calls bilu_pattern_upload, bilu_pattern_schedule and
+ *    bilu_symbolic_gpu, never in factor, apply, SpMV or solve; those read the
+ *    pattern's device copy and schedules and modify nothing in the handle, so
+ *    several host threads may run them on one pattern at once (set-up calls
+ *    on that pattern must not overlap them).
  *  - Pointers prefixed d_ are device pointers on the current device; the
  *    others are host pointers.  Input and output vectors must not alias.
  *  - Every call returns a bilu_status code; no call aborts the process and no
@@ -105,11 +109,30 @@ int bilu_pattern_export(const bilu_pattern* p, int32_t* row_ptr, int32_t* col_id
 
 /*
  * bilu_pattern_upload -- copy the pattern's integer structure to the current
- * device (set-up; allocates device memory owned by the handle, about
- * 4*(2n + nnz_l + nnz_u + nnz_a) bytes).  Synchronises the stream.  Needed
- * before bilu_factor, bilu_apply and bicgstab_solve.
+ * device and build the schedules of the sync-free factorization and solves
+ * (set-up; allocates device memory owned by the handle, about
+ * 4*(4n + nnz_l + nnz_u + nnz_a) bytes).  Synchronises the stream.  Needed
+ * before bilu_factor, bilu_apply and the solvers, which return
+ * BILU_ERR_STATE without it.
  */
 int bilu_pattern_upload(bilu_pattern* p, void* stream);
+
+/*
+ * bilu_pattern_schedule -- rebuild the uploaded pattern's schedules with the
+ * current tuning settings (the chunk targets of include/bilu_tuning.h take
+ * effect here and in bilu_pattern_upload, nowhere else).  The paper has no
+ * counterpart: a schedule is how the sync-free kernels walk the Eq. 4
+ * dependency graph, not what they compute.  Set-up: synchronises the stream,
+ * allocates the new schedules before freeing the old ones (on failure the old
+ * ones stay), and must not overlap a compute call on the same pattern.
+ * BILU_ERR_STATE if the pattern is not uploaded to the current device.
+ */
+int bilu_pattern_schedule(bilu_pattern* p, void* stream);
+
+/* Rows per chunk of the current solve and factorization schedules (0 when
+ * there is none, e.g. before bilu_pattern_upload).  Either output may be
+ * NULL.  Host only. */
+int bilu_pattern_schedule_info(const bilu_pattern* p, int32_t* solve_rows, int32_t* factor_rows);
 
 /* Frees the handle and its device copy.  NULL is ignored. */
 void bilu_destroy_pattern(bilu_pattern* p);
@@ -174,7 +197,9 @@ size_t bilu_apply_workspace_bytes(const bilu_pattern* p, int32_t b);
  *   L y = r (rows ascending), z = D^{-1} y, U' x = z (rows descending).
  * z = D^{-1} y is a pass of its own between the two solves, in place in the
  * workspace.  Both triangular solves run as single sync-free kernels: each
- * row waits, with a bounded spin, for the rows it depends on.
+ * row waits, with a bounded spin, for the rows it depends on.  Allocates
+ * nothing and builds nothing: it runs on the schedule of the last
+ * bilu_pattern_upload / bilu_pattern_schedule (BILU_ERR_STATE if none).
  *   d_factors  device, output of bilu_factor with the same b
  *   d_r, d_x   device, n*b doubles each; must not alias
  *   d_work     device scratch of at least bilu_apply_workspace_bytes bytes
@@ -205,18 +230,30 @@ int bilu_workspace_status(const void* d_work, void* stream);
  *   Set-up: the first call on each device looks up the array's device
  *   address (with that device current); make that first call before any
  *   stream capture begins.  The pattern must have been uploaded
- *   (bilu_pattern_upload builds the solve order this call reuses; a chunk
- *   size set later with bilu_set_trisolve_chunk is not applied here).
+ *   (bilu_pattern_upload / bilu_pattern_schedule build the solve order this
+ *   call reuses, as bilu_apply does).
  *   Sharing: every call uses the same array, whose contents persist between
  *   calls; each call resets what must start cleared before use.  Calls whose
  *   work overlaps on the GPU (different streams, other threads) race on the
  *   array and give wrong results: serialise them.
  *   Arguments as for bilu_apply, without the workspace.  Asynchronous; a
  *   bounded dependency wait that runs out (which correct use never causes)
- *   is not reported by this call.
+ *   is recorded in the scratch's error word: bilu_apply_noalloc_status
+ *   reads it.
  */
 int bilu_apply_noalloc(const bilu_pattern* p, int32_t b, const double* d_factors, const double* d_r,
                        double* d_x, void* stream);
+
+/*
+ * bilu_apply_noalloc_status -- synchronises the stream and returns the status
+ * the most recent bilu_apply_noalloc on the current device recorded in the
+ * fixed scratch's error word: BILU_OK, or BILU_ERR_TIMEOUT when a bounded
+ * dependency wait ran out (x then holds NaN where rows were not solved).
+ * Allocates nothing; reads 4 bytes through the scratch address the first
+ * bilu_apply_noalloc on this device looked up (BILU_ERR_STATE before any
+ * such call).  The paper has no counterpart.
+ */
+int bilu_apply_noalloc_status(void* stream);
 
 /* ------------------------------------------------------------------------ */
 /* Block SpMV (device)                                                       */

@@ -24,8 +24,9 @@ extern "C" {
  * rows that do not depend on their predecessor: grid-line starts in a
  * natural ordering), 2 L instead -- two grid lines per chunk; 1 <= rows <=
  * 1024 fixes the target;
- * other values: BILU_ERR_ARG.  The schedule is rebuilt (host work plus one
- * device allocation) by the next apply or solve on each pattern. */
+ * other values: BILU_ERR_ARG.  Takes effect for a pattern at its next
+ * bilu_pattern_upload or bilu_pattern_schedule (the set-up calls that build
+ * schedules); apply, factor and solve never rebuild one. */
 int bilu_set_trisolve_chunk(int32_t rows);
 int32_t bilu_get_trisolve_chunk(void);
 
@@ -38,7 +39,8 @@ int32_t bilu_auto_trisolve_chunk(const bilu_pattern* p);
  * or 3 L (three grid lines) where that hits 256 and a line length L of
  * 16..128 rows is detected (see bilu_set_trisolve_chunk);
  * 1 <= rows <= 1024 fixes it; other values: BILU_ERR_ARG.  Its schedule is
- * separate from the solves' and is rebuilt by the next factorization. */
+ * separate from the solves'; like theirs it is built by bilu_pattern_upload
+ * and bilu_pattern_schedule only. */
 int bilu_set_factor_chunk(int32_t rows);
 int32_t bilu_get_factor_chunk(void);
 
@@ -48,12 +50,12 @@ int32_t bilu_auto_factor_chunk(const bilu_pattern* p);
 
 /* Warps per CTA in the triangular solves: 4 (default), 8 or 16, else
  * BILU_ERR_ARG.  More warps per chunk give each row more time to fetch its
- * operands ahead of its dependencies. */
+ * operands ahead of its dependencies.  Applies to the next launch. */
 int bilu_set_trisolve_warps(int32_t warps);
 
 /* Host copy of the schedule the sync-free solves use for a target of `rows`
- * rows per chunk (the same one bilu_apply builds; the factorization builds
- * one the same way for its own target).  Rows are cut into *nchunks chunks
+ * rows per chunk (the same one bilu_pattern_upload / bilu_pattern_schedule
+ * build; the factorization builds one the same way for its own target).  Rows are cut into *nchunks chunks
  * of consecutive rows, chunk c = rows [bounds[c], bounds[c+1]).  A cut falls
  * before the row farthest from its nearest dependency (the largest gap
  * r - max{j < r in L(r)}, and likewise for U') among the rows with a gap > 1

@@ -60,6 +60,9 @@ SIGNATURES = {
     "bilu_apply": (C.c_int, [_vp, C.c_int32, _vp, _vp, _vp, _vp, C.c_size_t, _vp]),
     "bilu_workspace_status": (C.c_int, [_vp, _vp]),
     "bilu_apply_noalloc": (C.c_int, [_vp, C.c_int32, _vp, _vp, _vp, _vp]),
+    "bilu_apply_noalloc_status": (C.c_int, [_vp]),
+    "bilu_pattern_schedule": (C.c_int, [_vp, _vp]),
+    "bilu_pattern_schedule_info": (C.c_int, [_vp, _i32p, _i32p]),
     "bsr_spmv": (C.c_int, [C.c_int32, C.c_int32, _vp, _vp, _vp, _vp, _vp, _vp]),
     "bicgstab_workspace_bytes": (C.c_size_t, [_vp, C.c_int32]),
     "bicgstab_solve": (C.c_int, [_vp, C.POINTER(BSR), _vp, _vp, _vp, C.c_double, C.c_int32, _vp,

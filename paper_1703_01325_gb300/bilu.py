@@ -83,9 +83,24 @@ class Pattern:
         return dict(row_ptr=rp, col_idx=ci[:nnz], lev=lev[:nnz], lvl_lower=lo[:n], lvl_upper=up[:n])
 
     def upload(self, stream=None):
+        """bilu_pattern_upload: the device copy and the schedules."""
         _check(L.load().bilu_pattern_upload(self.handle, _stream_handle(stream)), "bilu_pattern_upload")
         self.uploaded = True
         return self
+
+    def reschedule(self, stream=None):
+        """bilu_pattern_schedule: rebuild the schedules with the current tuning
+        settings (chunk targets)."""
+        _check(L.load().bilu_pattern_schedule(self.handle, _stream_handle(stream)), "bilu_pattern_schedule")
+        return self
+
+    def schedule_info(self) -> dict:
+        """bilu_pattern_schedule_info: rows per chunk of the current solve and
+        factorization schedules."""
+        sr, fr = C.c_int32(), C.c_int32()
+        _check(L.load().bilu_pattern_schedule_info(self.handle, C.byref(sr), C.byref(fr)),
+               "bilu_pattern_schedule_info")
+        return {"solve_rows": sr.value, "factor_rows": fr.value}
 
     def schedule(self, rows: int) -> dict:
         """The sync-free solve schedule for a target of `rows` rows per chunk
@@ -226,6 +241,12 @@ def bilu_apply_noalloc(pattern: Pattern, b: int, factors: torch.Tensor, r: torch
     return L.load().bilu_apply_noalloc(pattern.handle, b, _dev(factors, torch.float64, "factors"),
                                        _dev(r, torch.float64, "r"), _dev(x, torch.float64, "x"),
                                        _stream_handle(stream))
+
+
+def bilu_apply_noalloc_status(stream=None) -> int:
+    """Status the last bilu_apply_noalloc on the current device recorded in the
+    fixed scratch (synchronises the stream; allocates nothing)."""
+    return L.load().bilu_apply_noalloc_status(_stream_handle(stream))
 
 
 def bilu_workspace_status(work: torch.Tensor, stream=None) -> int:

@@ -15,13 +15,18 @@ namespace {
 
 bool valid_b(int32_t b) { return b >= 1 && b <= 8; }
 
-// The schedules the factorization and the solves run on, rebuilt (host work
-// plus one device allocation) when the chunk target changed.
+// The schedules the factorization and the solves run on exist once the
+// pattern is uploaded; only bilu_pattern_upload and bilu_pattern_schedule
+// (re)build them.  The compute calls never do.
 int solve_schedule(const bilu_pattern* p) {
-  return ensure_schedule(p, &const_cast<bilu_pattern*>(p)->solve, solve_chunk_target(p), true);
+  return (p->n == 0 || (p->solve.d_mem && p->solve.upper)) ? BILU_OK : BILU_ERR_STATE;
 }
-int factor_schedule(const bilu_pattern* p) {
-  return ensure_schedule(p, &const_cast<bilu_pattern*>(p)->fact, factor_chunk_target(p), false);
+int factor_schedule(const bilu_pattern* p) { return (p->n == 0 || p->fact.d_mem) ? BILU_OK : BILU_ERR_STATE; }
+
+int build_schedules(bilu_pattern* p) {
+  if (make_schedule(p, &p->solve, solve_chunk_target(p), true) != 0) return BILU_ERR_OOM;
+  if (!p->is_transpose && make_schedule(p, &p->fact, factor_chunk_target(p), false) != 0) return BILU_ERR_OOM;
+  return BILU_OK;
 }
 
 int ready(const bilu_pattern* p) {
@@ -101,9 +106,22 @@ extern "C" int bilu_pattern_upload(bilu_pattern* p, void* stream) {
   }
   p->d_mem = mem;
   p->device = dev;
-  if (ensure_schedule(p, &p->solve, solve_chunk_target(p), true) != 0 ||
-      (!p->is_transpose && ensure_schedule(p, &p->fact, factor_chunk_target(p), false) != 0))
-    return BILU_ERR_OOM;
+  return build_schedules(p);
+}
+
+extern "C" int bilu_pattern_schedule(bilu_pattern* p, void* stream) {
+  if (!p) return BILU_ERR_ARG;
+  int st = ready(p);
+  if (st) return st;
+  if (p->n == 0) return BILU_OK;
+  if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) return BILU_ERR_CUDA;
+  return build_schedules(p);
+}
+
+extern "C" int bilu_pattern_schedule_info(const bilu_pattern* p, int32_t* solve_rows, int32_t* factor_rows) {
+  if (!p) return BILU_ERR_ARG;
+  if (solve_rows) *solve_rows = p->solve.d_mem ? p->solve.chunk : 0;
+  if (factor_rows) *factor_rows = p->fact.d_mem ? p->fact.chunk : 0;
   return BILU_OK;
 }
 
@@ -140,7 +158,7 @@ int factor_impl(const bilu_pattern* p, int32_t b, const double* d_a_vals, TV* d_
   if (st) return st;
   if (p->n > 0 && (!d_a_vals || !d_factors || !d_work)) return BILU_ERR_ARG;
   if (work_bytes < bilu_factor_workspace_bytes(p, b)) return BILU_ERR_STATE;
-  if (factor_schedule(p) != 0) return BILU_ERR_OOM;
+  if (factor_schedule(p) != BILU_OK) return BILU_ERR_STATE;
   cudaStream_t s = (cudaStream_t)stream;
   int32_t* header = (int32_t*)d_work;
   int32_t* done = (int32_t*)((char*)d_work + kHeaderBytes);
@@ -202,7 +220,7 @@ extern "C" int bilu_apply(const bilu_pattern* p, int32_t b, const double* d_fact
   if (p->n == 0) return BILU_OK;
   if (!d_factors || !d_r || !d_x || !d_work || (const void*)d_r == (const void*)d_x) return BILU_ERR_ARG;
   if (work_bytes < apply_workspace_bytes(p->n, b)) return BILU_ERR_STATE;
-  if (solve_schedule(p) != 0) return BILU_ERR_OOM;
+  if (solve_schedule(p) != BILU_OK) return BILU_ERR_STATE;
   return cuda_status(launch_apply(p, b, d_factors, d_r, d_x, d_work, nullptr, stream));
 }
 
@@ -253,7 +271,7 @@ extern "C" int bicgstab_solve(const bilu_pattern* p, const bilu_bsr* A, const do
       (const void*)d_rhs == (const void*)d_x)
     return BILU_ERR_ARG;
   if (work_bytes < krylov_workspace_bytes(p->n, A->b)) return BILU_ERR_STATE;
-  if (solve_schedule(p) != 0) return BILU_ERR_OOM;
+  if (solve_schedule(p) != BILU_OK) return BILU_ERR_STATE;
   return run_bicgstab(p, A, d_factors, d_rhs, d_x, tol, maxit, d_work, stream, info, g_check_every);
 }
 
@@ -277,7 +295,7 @@ extern "C" int bicgstab_solve_f32prec(const bilu_pattern* p, const bilu_bsr* A, 
       (const void*)d_rhs == (const void*)d_x)
     return BILU_ERR_ARG;
   if (work_bytes < krylov_workspace_bytes(p->n, A->b)) return BILU_ERR_STATE;
-  if (solve_schedule(p) != 0) return BILU_ERR_OOM;
+  if (solve_schedule(p) != BILU_OK) return BILU_ERR_STATE;
   return run_bicgstab(p, A, nullptr, d_rhs, d_x, tol, maxit, d_work, stream, info, g_check_every, d_factors32);
 }
 
@@ -308,7 +326,7 @@ extern "C" int gmres_solve(const bilu_pattern* p, const bilu_bsr* A, const doubl
       (const void*)d_rhs == (const void*)d_x)
     return BILU_ERR_ARG;
   if (work_bytes < gmres_workspace_bytes_impl(p->n, A->b, restart)) return BILU_ERR_STATE;
-  if (solve_schedule(p) != 0) return BILU_ERR_OOM;
+  if (solve_schedule(p) != BILU_OK) return BILU_ERR_STATE;
   return run_gmres(p, A, d_factors, d_rhs, d_x, tol, maxit, restart, d_work, stream, info, g_check_every);
 }
 
@@ -332,7 +350,7 @@ extern "C" int bilu_apply_f32(const bilu_pattern* p, int32_t b, const float* d_f
   if (p->n == 0) return BILU_OK;
   if (!d_factors32 || !d_r || !d_x || !d_work || (const void*)d_r == (const void*)d_x) return BILU_ERR_ARG;
   if (work_bytes < apply_workspace_bytes(p->n, b)) return BILU_ERR_STATE;
-  if (solve_schedule(p) != 0) return BILU_ERR_OOM;
+  if (solve_schedule(p) != BILU_OK) return BILU_ERR_STATE;
   return cuda_status(launch_apply_f32(p, b, d_factors32, d_r, d_x, d_work, nullptr, stream));
 }
 
@@ -373,7 +391,7 @@ extern "C" int bicgstab_solve_mixed(const bilu_pattern* p, const bilu_bsr* A, co
       (const void*)d_rhs == (const void*)d_x)
     return BILU_ERR_ARG;
   if (work_bytes < krylov_mixed_workspace_bytes(p->n, A->b)) return BILU_ERR_STATE;
-  if (solve_schedule(p) != 0) return BILU_ERR_OOM;
+  if (solve_schedule(p) != BILU_OK) return BILU_ERR_STATE;
   return run_bicgstab_mixed(p, A, d_vals32, d_factors32, d_rhs, d_x, tol, maxit, inner_tol, inner_maxit,
                             d_work, stream, info, g_check_every);
 }

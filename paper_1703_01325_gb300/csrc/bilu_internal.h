@@ -141,8 +141,9 @@ int launch_scale_upper_f32(const bilu_pattern* p, int32_t b, float* f, void* str
 
 size_t apply_workspace_bytes(int32_t n, int32_t b);
 // Builds (host) and uploads schedule *s for `chunk` rows per chunk (the U'
-// part only if `upper`); nothing happens if it is current.
-int ensure_schedule(const bilu_pattern* p, bilu_chunk_schedule* s, int32_t chunk, bool upper);
+// part only if `upper`).  Allocates device memory and synchronises; the
+// previous schedule is freed only once the new one is in place.
+int make_schedule(const bilu_pattern* p, bilu_chunk_schedule* s, int32_t chunk, bool upper);
 // Host part (symbolic.cpp).
 void build_schedule(const bilu_pattern* p, int32_t chunk, bool upper, bilu_chunk_schedule* s);
 // Eq. 4 levels, L / U' split and backfill map of a pattern with rp, ci, lev set.

@@ -69,3 +69,24 @@ extern "C" int bilu_apply_noalloc(const bilu_pattern* p, int32_t b, const double
   return bilu::launch_apply(p, b, d_factors, d_r, d_x, scratch, nullptr, stream) == 0 ? BILU_OK
                                                                                      : BILU_ERR_CUDA;
 }
+
+// Status of the last bilu_apply_noalloc on the current device: the error word
+// of the fixed scratch's header, copied out (4 bytes) after the stream's work.
+// Uses only the address bilu_apply_noalloc cached; allocates nothing.
+extern "C" int bilu_apply_noalloc_status(void* stream) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return BILU_ERR_CUDA;
+  void* base = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_scratch_mu);
+    base = g_scratch_addr[dev];
+  }
+  if (!base) return BILU_ERR_STATE;
+  int32_t err = 0;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (cudaMemcpyAsync(&err, reinterpret_cast<const int32_t*>(base) + bilu::kErr, sizeof(err),
+                      cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return BILU_ERR_CUDA;
+  return err;
+}

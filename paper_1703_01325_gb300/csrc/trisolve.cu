@@ -481,36 +481,44 @@ void free_schedule(bilu_chunk_schedule* s) {
   s->chunk = 0;
 }
 
-int ensure_schedule(const bilu_pattern* p, bilu_chunk_schedule* s, int32_t chunk, bool upper) {
-  if (s->chunk == chunk && (s->upper || !upper) && (s->d_mem || p->n == 0)) return 0;
+int make_schedule(const bilu_pattern* p, bilu_chunk_schedule* s, int32_t chunk, bool upper) {
+  bilu_chunk_schedule t;
+  build_schedule(p, chunk, upper, &t);
+  if (p->n > 0) {
+    const size_t one = align256(sizeof(int32_t) * (size_t)p->n);
+    const size_t tk = align256(sizeof(int32_t) * (size_t)t.nchunks);
+    const size_t bd = align256(sizeof(int32_t) * ((size_t)t.nchunks + 1));
+    const int parts = upper ? 2 : 1;
+    void* mem = nullptr;
+    if (cudaMalloc(&mem, bd + parts * (one + tk)) != cudaSuccess) {
+      cudaGetLastError();
+      return (int)cudaErrorMemoryAllocation;
+    }
+    char* m = (char*)mem;
+    t.d_mem = mem;
+    t.d_bnd = (int32_t*)m;
+    m += bd;
+    auto put = [&](int32_t*& dst, const std::vector<int32_t>& v, size_t bytes) {
+      dst = (int32_t*)m;
+      m += bytes;
+      cudaMemcpy(dst, v.data(), sizeof(int32_t) * v.size(), cudaMemcpyHostToDevice);
+    };
+    cudaMemcpy(t.d_bnd, t.bnd.data(), sizeof(int32_t) * t.bnd.size(), cudaMemcpyHostToDevice);
+    put(t.d_ord_l, t.ord_l, one);
+    put(t.d_tick_l, t.tick_l, tk);
+    if (upper) {
+      put(t.d_ord_u, t.ord_u, one);
+      put(t.d_tick_u, t.tick_u, tk);
+    }
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+      cudaFree(mem);
+      return (int)e;
+    }
+  }
   free_schedule(s);
-  build_schedule(p, chunk, upper, s);
-  if (p->n == 0) return 0;
-  const size_t one = align256(sizeof(int32_t) * (size_t)p->n);
-  const size_t tk = align256(sizeof(int32_t) * (size_t)s->nchunks);
-  const size_t bd = align256(sizeof(int32_t) * ((size_t)s->nchunks + 1));
-  const int parts = upper ? 2 : 1;
-  void* mem = nullptr;
-  if (cudaMalloc(&mem, bd + parts * (one + tk)) != cudaSuccess) {
-    cudaGetLastError();
-    s->chunk = 0;
-    return (int)cudaErrorMemoryAllocation;
-  }
-  char* m = (char*)mem;
-  s->d_mem = mem;
-  s->d_bnd = (int32_t*)m;
-  s->d_ord_l = (int32_t*)(m + bd);
-  s->d_tick_l = (int32_t*)(m + bd + one);
-  cudaMemcpy(s->d_bnd, s->bnd.data(), sizeof(int32_t) * s->bnd.size(), cudaMemcpyHostToDevice);
-  cudaMemcpy(s->d_ord_l, s->ord_l.data(), sizeof(int32_t) * p->n, cudaMemcpyHostToDevice);
-  cudaMemcpy(s->d_tick_l, s->tick_l.data(), sizeof(int32_t) * s->tick_l.size(), cudaMemcpyHostToDevice);
-  if (upper) {
-    s->d_ord_u = (int32_t*)(m + bd + one + tk);
-    s->d_tick_u = (int32_t*)(m + bd + 2 * one + tk);
-    cudaMemcpy(s->d_ord_u, s->ord_u.data(), sizeof(int32_t) * p->n, cudaMemcpyHostToDevice);
-    cudaMemcpy(s->d_tick_u, s->tick_u.data(), sizeof(int32_t) * s->tick_u.size(), cudaMemcpyHostToDevice);
-  }
-  return (int)cudaGetLastError();
+  *s = std::move(t);
+  return 0;
 }
 
 size_t apply_workspace_bytes(int32_t n, int32_t b) {

@@ -31,3 +31,35 @@ def test_exports_every_declared_symbol(libbilu):
 def test_library_is_sm103a_build():
     from paper_1703_01325_gb300 import build
     assert build.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
+
+
+def test_compute_calls_never_build_a_schedule(libbilu):
+    """Schedules come from the set-up calls only (bilu_pattern_upload,
+    bilu_pattern_schedule).  On a pattern that was never uploaded, a new chunk
+    setting followed by factor, apply and solve calls leaves the pattern
+    without schedules and every call returns BILU_ERR_STATE before touching a
+    device (no CUDA call is made on this path, so it runs without a GPU)."""
+    import ctypes as C
+
+    import paper_1703_01325_gb300.bilu as B
+    from paper_1703_01325_gb300 import _lib as L
+    from paper_1703_01325_gb300.reservoir import grid_pattern
+    rp, ci = grid_pattern(6, 5, 4, 7)
+    P = B.bilu_symbolic(120, rp, ci, 1)
+    lib = L.load()
+    fake = C.c_void_p(0x1000)  # never dereferenced: the state check comes first
+    old = B.bilu_get_trisolve_chunk()
+    try:
+        B.bilu_set_trisolve_chunk(17)
+        assert P.schedule_info() == {"solve_rows": 0, "factor_rows": 0}
+        assert lib.bilu_apply(P.handle, 3, fake, fake, C.c_void_p(0x2000), fake, 1 << 30, None) == L.BILU_ERR_STATE
+        info = L.FactorInfo()
+        assert lib.bilu_factor(P.handle, 3, fake, fake, fake, 1 << 30, None, C.byref(info)) == L.BILU_ERR_STATE
+        bsr = L.BSR(120, 3, fake, fake, fake)
+        si = L.SolveInfo()
+        assert lib.bicgstab_solve(P.handle, C.byref(bsr), fake, fake, C.c_void_p(0x2000), 1e-8, 10, fake, 1 << 30,
+                                  None, C.byref(si)) == L.BILU_ERR_STATE
+        assert lib.bilu_pattern_schedule(P.handle, None) == L.BILU_ERR_STATE
+        assert P.schedule_info() == {"solve_rows": 0, "factor_rows": 0}
+    finally:
+        B.bilu_set_trisolve_chunk(old)

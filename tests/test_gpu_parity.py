@@ -48,6 +48,7 @@ def _check_factor_apply(B, S, k, chunks=(32, 1024), factor_chunks=(None,)):
         for fch in factor_chunks:
             if fch is not None:
                 B.bilu_set_factor_chunk(fch)
+                P.reschedule()  # chunk settings take effect at set-up only
             F, info = B.bilu_factor(P, S.b, vals)
             assert info.status == 0
             Lg, Dg, Ug = (t.cpu().numpy() for t in B.factor_sections(P, S.b, F))
@@ -61,6 +62,8 @@ def _check_factor_apply(B, S, k, chunks=(32, 1024), factor_chunks=(None,)):
     try:
         for ch in chunks:
             B.bilu_set_trisolve_chunk(ch)
+            P.reschedule()
+            assert P.schedule_info()["solve_rows"] == ch
             work = B.workspace(P.apply_workspace_bytes(S.b))
             x = B.bilu_apply(P, S.b, F, rhs, work=work)
             assert B.bilu_workspace_status(work) == 0
@@ -116,6 +119,7 @@ def test_apply_row_widths(B, b, dims, k, width):
     try:
         for ch in (1, 32):
             B.bilu_set_trisolve_chunk(ch)
+            P.reschedule()
             x = B.bilu_apply(P, b, F, rhs).cpu().numpy()
             assert rel_maxerr(x, o.apply(S.rhs)) <= TOL_APPLY, ch
             x32 = B.bilu_apply_f32(P, b, B.bilu_convert_f32(F), rhs).cpu().numpy()
@@ -221,6 +225,7 @@ def test_dependency_wait_times_out_and_recovers(B):
     work = B.workspace(P.apply_workspace_bytes(3))
     old_chunk = B.bilu_get_trisolve_chunk()
     B.bilu_set_trisolve_chunk(16)  # row 5's dependent 5 + 80 lies in another chunk
+    P.reschedule()
     B.bilu_set_spin_limit_ns(20_000_000)
     B.bilu_test_withhold_row(5)
     try:
@@ -394,3 +399,46 @@ def test_apply_input_holding_the_pending_pattern(B, fp32):
     nan = np.isnan(x)
     assert nan.any() and not np.isnan(clean).any()
     assert np.array_equal(x[~nan], clean[~nan])
+
+
+def test_compute_calls_never_rebuild_the_schedule(B):
+    """Chunk settings take effect at set-up (bilu_pattern_upload /
+    bilu_pattern_schedule) only: an apply, a factorization and a solve after a
+    new setting run on the existing schedule and leave it as it is; the next
+    bilu_pattern_schedule applies the setting.  Every schedule gives the
+    oracle's x."""
+    S = reservoir_system(12, 10, 6, 3, seed=4)
+    o = OracleRun(S.n, 3, S.row_ptr, S.col_idx, S.vals, 1)
+    rp, ci, vals, rhs = device_system(S, DEV)
+    old_t, old_f = B.bilu_get_trisolve_chunk(), B.bilu_get_factor_chunk()
+    try:
+        B.bilu_set_trisolve_chunk(40)
+        B.bilu_set_factor_chunk(60)
+        P = B.bilu_symbolic(S.n, S.row_ptr, S.col_idx, 1).upload()
+        assert P.schedule_info() == {"solve_rows": 40, "factor_rows": 60}
+        B.bilu_set_trisolve_chunk(13)
+        B.bilu_set_factor_chunk(17)
+        F, info = B.bilu_factor(P, 3, vals)
+        x = B.bilu_apply(P, 3, F, rhs)
+        _, si = B.bicgstab_solve(P, (S.n, 3, rp, ci, vals), F, rhs, tol=1e-10, maxit=300)
+        assert info.status == 0 and si.status == 0
+        assert P.schedule_info() == {"solve_rows": 40, "factor_rows": 60}
+        assert rel_maxerr(x.cpu().numpy(), o.apply(S.rhs)) <= TOL_APPLY
+        P.reschedule()
+        assert P.schedule_info() == {"solve_rows": 13, "factor_rows": 17}
+        F2, _ = B.bilu_factor(P, 3, vals)
+        assert rel_maxerr(B.bilu_apply(P, 3, F2, rhs).cpu().numpy(), o.apply(S.rhs)) <= TOL_APPLY
+    finally:
+        B.bilu_set_trisolve_chunk(old_t)
+        B.bilu_set_factor_chunk(old_f)
+
+
+def test_compute_calls_need_an_uploaded_pattern(B):
+    S = reservoir_system(6, 5, 4, 3, seed=1)
+    rp, ci, vals, rhs = device_system(S, DEV)
+    P = B.bilu_symbolic(S.n, S.row_ptr, S.col_idx, 1)
+    assert P.schedule_info() == {"solve_rows": 0, "factor_rows": 0}
+    from paper_1703_01325_gb300 import _lib as L
+    with pytest.raises(B.BiluError) as e:
+        B.bilu_factor(P, 3, vals)
+    assert e.value.status == L.BILU_ERR_STATE

@@ -1,6 +1,7 @@
-"""The device symbolic phase (bilu_symbolic_gpu) against the host one: P', the
-level of every entry and both Eq. 4 level sets must agree bit for bit (the
-host phase is itself bit-exact with the oracle, test_symbolic_lib.py)."""
+"""The device symbolic phase (bilu_symbolic_gpu) against the CPU oracle: P'
+(Algorithm 3, Eq. 1-2), the level of fill of every entry and both Eq. 4
+level sets must agree bit for bit with oracle.symbolic / oracle.levels, and
+with the library's host phase."""
 from __future__ import annotations
 
 import numpy as np
@@ -8,6 +9,7 @@ import pytest
 
 torch = pytest.importorskip("torch")
 
+import oracle  # noqa: E402
 from paper_1703_01325_gb300.reservoir import grid_pattern, random_pattern  # noqa: E402
 
 pytestmark = pytest.mark.gpu
@@ -20,11 +22,29 @@ def B(libbilu):
     return B
 
 
-def _same(B, n, rp, ci, k, cap=256):
-    h = B.bilu_symbolic(n, rp, ci, k).export()
-    g = B.bilu_symbolic_gpu(n, rp, ci, k, row_capacity=cap).export()
+def _oracle_pattern(n, rp, ci, k):
+    prp, pci, plev = oracle.symbolic(n, rp, ci, k)
+    lo, up = oracle.levels(n, prp, pci)
+    return dict(row_ptr=prp, col_idx=pci, lev=plev, lvl_lower=lo, lvl_upper=up)
+
+
+def _same(B, n, rp, ci, k, cap=256, host=True):
+    P = B.bilu_symbolic_gpu(n, rp, ci, k, row_capacity=cap)
+    g = P.export()
+    o = _oracle_pattern(n, rp, ci, k)
     for key in ("row_ptr", "col_idx", "lev", "lvl_lower", "lvl_upper"):
-        assert np.array_equal(h[key], g[key]), key
+        assert np.array_equal(np.asarray(o[key], np.int32), g[key]), key
+    info = P.info
+    rows = np.repeat(np.arange(n), np.diff(o["row_ptr"]))
+    assert info.nnz_p == len(o["col_idx"]) and info.nnz_a == rp[-1]
+    assert info.nnz_l == int((o["col_idx"] < rows).sum()) and info.nnz_u == int((o["col_idx"] > rows).sum())
+    assert info.nlev_l == (o["lvl_lower"].max() + 1 if n else 0)
+    assert info.nlev_u == (o["lvl_upper"].max() + 1 if n else 0)
+    if host:
+        h = B.bilu_symbolic(n, rp, ci, k).export()
+        for key in ("row_ptr", "col_idx", "lev", "lvl_lower", "lvl_upper"):
+            assert np.array_equal(h[key], g[key]), key
+    return P
 
 
 @pytest.mark.parametrize("seed", range(10))
@@ -66,6 +86,13 @@ def test_capacity_and_pattern_errors(B):
 
 
 def test_full_size_workload(B):
-    """The 128 x 128 x 64 7-point pattern at ILU(1)."""
+    """The 128 x 128 x 64 7-point pattern at ILU(1) (the bench workload)."""
     rp, ci = grid_pattern(128, 128, 64, 7)
-    _same(B, 128 * 128 * 64, rp, ci, 1, cap=64)
+    _same(B, 128 * 128 * 64, rp, ci, 1, cap=64, host=False)
+
+
+def test_27pt_ilu2_workload(B):
+    """A 64 x 64 x 32 27-point pattern at ILU(2): rows of P' up to 125 blocks,
+    the fill structure of the 160 x 160 x 80 27-point ILU(2) case."""
+    rp, ci = grid_pattern(64, 64, 32, 27)
+    _same(B, 64 * 64 * 32, rp, ci, 2, cap=256, host=False)

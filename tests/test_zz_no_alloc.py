@@ -34,8 +34,36 @@ def test_noalloc_matches_workspace_apply(libbilu, grid, b, k):
     for r, ref in ((rhs, x_ref), (r2, x_ref2)):
         x = torch.full_like(rhs, float("nan"))
         assert B.bilu_apply_noalloc(P, b, F, r, x) == 0
+        assert B.bilu_apply_noalloc_status() == 0
         torch.cuda.synchronize()
         assert rel_maxerr(x.cpu().numpy(), ref.cpu().numpy()) <= TOL_APPLY
+
+
+def test_noalloc_reports_a_timed_out_wait(libbilu):
+    """A wait that runs out inside bilu_apply_noalloc is reported by
+    bilu_apply_noalloc_status (the test hook withholds one row of the lower
+    solve, so its dependents' bounded waits run out); the next call starts
+    from a clean error word and succeeds."""
+    import paper_1703_01325_gb300.bilu as B
+    torch.cuda.set_device(0)
+    S = reservoir_system(10, 8, 6, 3, sigma=1.0, accum=0.01, seed=2)
+    rp, ci, vals, rhs = device_system(S, "cuda:0")
+    P = B.bilu_symbolic(S.n, S.row_ptr, S.col_idx, 1).upload()
+    F, _ = B.bilu_factor(P, 3, vals)
+    x_ref = B.bilu_apply(P, 3, F, rhs)
+    x = torch.empty_like(rhs)
+    B.bilu_set_spin_limit_ns(20_000_000)
+    B.bilu_test_withhold_row(5)
+    try:
+        assert B.bilu_apply_noalloc(P, 3, F, rhs, x) == 0
+        assert B.bilu_apply_noalloc_status() == 6
+    finally:
+        B.bilu_test_withhold_row(-1)
+        B.bilu_set_spin_limit_ns(2_000_000_000)
+    assert B.bilu_apply_noalloc(P, 3, F, rhs, x) == 0
+    assert B.bilu_apply_noalloc_status() == 0
+    torch.cuda.synchronize()
+    assert rel_maxerr(x.cpu().numpy(), x_ref.cpu().numpy()) <= TOL_APPLY
 
 
 def test_noalloc_rejects_systems_beyond_the_fixed_scratch(libbilu):
