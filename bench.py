@@ -190,8 +190,8 @@ def cpu_baseline(S, k, gpu_iters, sample_iters=4):
     t5 = time.perf_counter()
     oracle.apply(S.n, S.b, prp, pci, F, D, S.rhs)
     t6 = time.perf_counter()
-    return {"value": round(value, 1), "unit": "ms", "cores": 1, "kind": "oracle",
-            "cpu_model": cpu_model(), "nproc": os.cpu_count(),
+    return {"value": round(value, 1), "unit": "ms", "cores": 1, "kind": "oracle", "estimate": True,
+            "sample_iters": sample_iters, "cpu_model": cpu_model(), "nproc": os.cpu_count(),
             "kernels_ms": {"symbolic": round(1e3 * (t1 - t0), 1), "factor": round(factor_ms, 1),
                            "spmv": round(1e3 * (t5 - t4), 1), "apply": round(1e3 * (t6 - t5), 1)},
             "sample": (f"oracle factorization of the full matrix ({factor_ms:.0f} ms) + {sample_iters} "
@@ -292,13 +292,101 @@ def run_reference(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": args.workload, "k": args.k, "tol": args.tol, "maxit": args.maxit, **cfg,
                    "step": "backfill + factor + BiCGSTAB iterations up to maxit"},
-        "cpu_baseline": {"value": round(ms, 1), "unit": "ms", "cores": 1, "kind": "oracle",
-                         "cpu_model": cpu_model(), "nproc": os.cpu_count(),
-                         "sample": f"per step: full factorization + {sample_iters} BiCGSTAB iterations, "
-                                   f"scaled to {iters_ref} iterations"},
+        "estimate": True,
+        "cpu_baseline": {"value": round(ms, 1), "unit": "ms", "cores": 1, "kind": "oracle", "estimate": True,
+                         "sample_iters": sample_iters, "cpu_model": cpu_model(), "nproc": os.cpu_count(),
+                         "sample": f"per step: full factorization + {sample_iters} BiCGSTAB iterations timed, "
+                                   f"the iterations scaled to {iters_ref}: the value is an estimate"},
         "e2e": {"value": round(ms, 1), "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(out), flush=True)
+
+
+def oracle_solution(S, k, tol=1e-12, maxit=600):
+    """The CPU oracle's FP64 solution of S (symbolic, backfill, factor and
+    BiCGSTAB toward `tol`, one thread): the reference every GPU solution's
+    error is stated against."""
+    import oracle
+    t0 = time.perf_counter()
+    prp, pci, _ = oracle.symbolic(S.n, S.row_ptr, S.col_idx, k)
+    F, D = oracle.factor(S.n, S.b, prp, pci, oracle.backfill(S.n, S.b, S.row_ptr, S.col_idx, S.vals, prp, pci))
+    x, it, rr, st = oracle.bicgstab(S.n, S.b, S.row_ptr, S.col_idx, S.vals, prp, pci, F, D, S.rhs, tol=tol,
+                                    maxit=maxit)
+    return {"x": x, "iters": int(it), "true_relres": float(rr), "status": int(st),
+            "seconds": round(time.perf_counter() - t0, 1)}
+
+
+def rel_err(x, ref) -> float:
+    """||x - ref|| / ||ref|| (2-norms, x a device or host vector)."""
+    import numpy as np
+    xv = x.cpu().numpy() if hasattr(x, "cpu") else np.asarray(x)
+    return float(np.linalg.norm(xv - ref) / np.linalg.norm(ref))
+
+
+def fp64_issue_ceiling(P, b, sms, sm_mhz, cycles_per_instr=19.0):
+    """Lower bound on each FP64 sweep's time from FP64 issue alone: the solve
+    kernel spreads a row's blocks over G groups of b lanes (the fewest that
+    hold the widest row, at least a quarter of the 32 // b), each lane does b
+    DFMAs per block it takes and log2(G) shuffle-add steps sum the groups,
+    so a row of m blocks costs ceil(m / G) * b + log2(G) FP64 warp
+    instructions; this part issues one FP64 warp instruction per ~19 cycles
+    per SM (measured), with the rows spread evenly over the SMs."""
+    import math
+    import numpy as np
+    e = P.export()
+    rp, ci = e["row_ptr"], e["col_idx"]
+    rows = np.repeat(np.arange(P.n), np.diff(rp))
+    gfull = 32 if b == 1 else 16 if b == 2 else 8 if b <= 4 else 4
+    out = {}
+    for name, mask in (("lower_solve", ci < rows), ("upper_solve", ci > rows)):
+        m = np.bincount(rows[mask], minlength=P.n)
+        need = int(m.max()) if P.n else 0
+        g = gfull // 4 if need <= gfull // 4 else gfull // 2 if need <= gfull // 2 else gfull
+        instr = np.ceil(m / g) * b + math.log2(g)
+        per_sm = instr.sum() / sms
+        out[name] = {"groups": g, "fp64_instr_per_row": round(float(instr.mean()), 3),
+                     "ceiling_us": round(per_sm * cycles_per_instr / sm_mhz, 1)}
+    return out
+
+
+def ms_to_tol_c2(B, dev, stream, b=3, k=1, reps=3, tol=1e-8, ref=None):
+    """Factor + FP64 BiCGSTAB from x0 = 0 to a true relative residual of 1e-8
+    on the 96 x 96 x 48 7-point workload (b = 3, ILU(1); inputs larger than
+    L2), timed like the step (CUDA events, median of `reps`), with the
+    solution's error against the CPU oracle's FP64 solution."""
+    import torch
+    from paper_1703_01325_gb300.reservoir import WORKLOADS, reservoir_system
+    S = reservoir_system(b=b, **WORKLOADS["grid96x96x48_7pt"])
+    P = B.bilu_symbolic(S.n, S.row_ptr, S.col_idx, k).upload()
+    rp, ci = torch.from_numpy(S.row_ptr).to(dev), torch.from_numpy(S.col_idx).to(dev)
+    vals, rhs = torch.from_numpy(S.vals.reshape(-1)).to(dev), torch.from_numpy(S.rhs).to(dev)
+    F = B.new_factors(P, b, dev)
+    fw = B.workspace(P.factor_workspace_bytes(b), dev)
+    sw = B.workspace(P.bicgstab_workspace_bytes(b), dev)
+    x = torch.zeros_like(rhs)
+    runs = []
+    for r in range(reps + 1):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        _, finfo = B.bilu_factor(P, b, vals, F, fw)
+        x.zero_()
+        _, info = B.bicgstab_solve(P, (S.n, b, rp, ci, vals), F, rhs, x=x, tol=tol, maxit=2000, work=sw)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if r:
+            runs.append((e0.elapsed_time(e1), finfo.ms, info))
+    runs.sort(key=lambda t: t[0])
+    ms, fms, info = runs[len(runs) // 2]
+    out = {"workload": "grid96x96x48_7pt", "b": b, "k": k, "tol": tol, "ms": round(ms, 2),
+           "factor_ms": round(fms, 2), "iters": info.iters, "true_relres": info.true_relres,
+           "status": info.status, "l2": "inputs larger than L2 (A values %.0f MB)" % (S.nnzb * b * b * 8 / 1e6)}
+    if ref is None:
+        ref = oracle_solution(S, k)
+    out["x_rel_err_vs_oracle"] = rel_err(x, ref["x"])
+    out["oracle_reference"] = {k2: ref[k2] for k2 in ("iters", "true_relres", "status", "seconds")}
+    P.close()
+    return out
 
 
 def ms_to_tol_small(B, dev, stream, reps=5):
@@ -330,7 +418,7 @@ def ms_to_tol_small(B, dev, stream, reps=5):
             "iters": info.iters, "true_relres": info.true_relres, "status": info.status}
 
 
-def precision_compare(B, dev, stream, cases=((2, 1), (4, 1)), tol=1e-8):
+def precision_compare(B, dev, stream, cases=((2, 1), (4, 1)), tol=1e-8, with_oracle=True):
     """Two FP32-preconditioner solvers against the plain FP64 solve
     (bilu_factor + bicgstab_solve), all from x0 = 0 to a true relative
     residual of `tol`, on the 96 x 96 x 48 7-point workload at block sizes b
@@ -341,8 +429,8 @@ def precision_compare(B, dev, stream, cases=((2, 1), (4, 1)), tol=1e-8):
     with the FP64 factors rounded to FP32 (bilu_factor + bilu_convert_f32);
     "fp64_gmres20" = the FP64 preconditioner in restarted GMRES(20), the
     solver of the paper's experiments (bilu_factor + gmres_solve).
-    Times include the factorization.  Each solution's distance to the FP64 one (which the parity
-    tests hold to the CPU oracle) is reported as its error."""
+    Times include the factorization.  Each solution's error is stated against
+    the CPU oracle's FP64 solution of the same system (BiCGSTAB to 1e-12)."""
     import torch
     from paper_1703_01325_gb300.reservoir import WORKLOADS, reservoir_system
     out = []
@@ -402,12 +490,15 @@ def precision_compare(B, dev, stream, cases=((2, 1), (4, 1)), tol=1e-8):
             torch.cuda.synchronize()
             row[name] = {"ms": round(e0.elapsed_time(e1), 2), "iters": si.iters, "true_relres": si.true_relres,
                          "status": si.status}
-        row["mixed_x_rel_err_vs_fp64"] = float((x32 - x64).norm() / x64.norm())
-        row["mixed_speedup"] = round(row["fp64"]["ms"] / row["mixed"]["ms"], 3)
-        row["f32prec_x_rel_err_vs_fp64"] = float((xp - x64).norm() / x64.norm())
-        row["f32prec_speedup"] = round(row["fp64"]["ms"] / row["f32prec"]["ms"], 3)
-        row["f32prec_from_fp64_x_rel_err_vs_fp64"] = float((xq - x64).norm() / x64.norm())
-        row["f32prec_from_fp64_speedup"] = round(row["fp64"]["ms"] / row["f32prec_from_fp64"]["ms"], 3)
+        ref = oracle_solution(S, k) if with_oracle else None
+        for name, xv in (("fp64", x64), ("mixed", x32), ("f32prec", xp), ("f32prec_from_fp64", xq),
+                         ("fp64_gmres20", xg)):
+            if ref is not None:
+                row[name]["x_rel_err_vs_oracle"] = rel_err(xv, ref["x"])
+            if name != "fp64":
+                row[name + "_speedup"] = round(row["fp64"]["ms"] / row[name]["ms"], 3)
+        if ref is not None:
+            row["oracle_reference"] = {k2: ref[k2] for k2 in ("iters", "true_relres", "status", "seconds")}
         out.append(row)
         P.close()
     return out
@@ -660,12 +751,13 @@ def main():
                "h2d_bytes_per_step": int(h_vals.numel() * 8 + h_rhs.numel() * 8),
                "d2h_bytes_per_step": int(h_x.numel() * 8)}
 
-    small = prec = f32 = None
+    small = prec = f32 = c2 = None
     if rank == 0 and args.workload == WORKLOAD and not args.no_extras:
         small = ms_to_tol_small(B, dev, stream)
+        c2 = ms_to_tol_c2(B, dev, stream)
         f32 = fp32_kernel_rates(B, S, P, F, vals, rhs, rp, ci, dev, stream)
         if not args.no_precision:
-            prec = precision_compare(B, dev, stream)
+            prec = precision_compare(B, dev, stream, with_oracle=not args.no_cpu)
     if rank != 0:
         if dist:
             dist.destroy_process_group()
@@ -676,6 +768,20 @@ def main():
     if not args.no_cpu and world == 1:
         cpu = cpu_baseline(S, args.k, gpu_iters)
     factor_ms = prof["backfill"][1] + prof["factor"][1] + prof["scale_upper"][1] + prof["factor_init"][1]
+    clk = clocks.summary()
+    ceil = None
+    if kern:
+        sm_mhz = clk.get("sm_mhz") or 2070.0
+        ceil = fp64_issue_ceiling(P, b, torch.cuda.get_device_properties(dev).multi_processor_count, sm_mhz)
+        for name in ("lower_solve", "upper_solve"):
+            if name in kern:
+                ceil[name]["measured_us"] = kern[name]["avg_us"]
+                ceil[name]["frac"] = round(ceil[name]["ceiling_us"] / kern[name]["avg_us"], 3)
+        ceil["note"] = ("FP64 issue bound of each FP64 sweep at the sampled SM clock: "
+                        "ceil(blocks/G)*b DFMA + log2(G) DADD warp instructions per row, "
+                        "one FP64 warp instruction per 19 cycles per SM; frac = ceiling / measured")
+    if roof is not None and ceil is not None and roof["kernel"] in ceil:
+        roof["fp64_issue_frac"] = ceil[roof["kernel"]]["frac"]
     out = {
         "metric": METRIC, "value": round(ms, 3), "unit": "ms", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms, 3), "higher_is_better": False, "scaling": "weak",
@@ -685,15 +791,18 @@ def main():
                    "trisolve_chunk": B.bilu_get_trisolve_chunk() or "auto (two grid lines on natural-order grids)",
                    "l2": "inputs larger than L2 (A values %.0f MB, factors %.0f MB)" % (
                        S.nnzb * b * b * 8 / 1e6, P.factor_bytes(b) / 1e6),
-                   "step": "backfill + factor + BiCGSTAB from x0 = 0 toward tol, at most maxit iterations"},
+                   "step": ("backfill + factor + BiCGSTAB from x0 = 0 toward tol, at most maxit iterations; "
+                            "this workload does not reach 1e-8 (nor does the CPU oracle), so a step is a "
+                            "fixed budget of maxit iterations: 'ms to 1e-8' is measured on the converging "
+                            "96x96x48 workload (ms_to_tol_c2) and on 16x16x8 (ms_to_tol_small)")},
         "converged": statuses == [0], "solve_status": statuses, "iters": gpu_iters,
         "true_relres": iters[-1][2],
         "factor_ms": round(factor_ms / args.steps, 3), "symbolic_ms": round(symbolic_ms, 1),
         "per_iteration_ms": round((ms - factor_ms / args.steps) / max(gpu_iters, 1), 4),
-        "ms_to_tol_small": small,
+        "ms_to_tol_small": small, "ms_to_tol_c2": c2, "fp64_issue": ceil,
         "fp32_prec_vs_fp64": prec, "fp32_kernels": f32,
         "kernels": kern, "roofline": roof, "e2e": e2e, "cpu_baseline": cpu,
-        "gpu_launches": int(launches), "clocks": clocks.summary(),
+        "gpu_launches": int(launches), "clocks": clk,
         "fp64_alu": {"peak_tflops": FP64_PEAK_TFLOPS,
                      "spmv_tflops": round(2 * S.nnzb * b * b / (kern["spmv"]["avg_us"] * 1e-6) / 1e12, 3)
                      if "spmv" in kern else None},
