@@ -419,10 +419,17 @@ int gmres_solve(const bilu_pattern* p, const bilu_bsr* A, const double* d_factor
 
 /*
  * bilu_symbolic_gpu -- the same P', fill levels and Eq. 4 levels as
- * bilu_symbolic (bit for bit), with the Algorithm 3 row merges run on the
- * current device: one warp per row, rows in ascending order, row i waiting
- * (bounded) for each pivot row p < i it merges.  Inputs are host arrays as for
- * bilu_symbolic; the returned handle is the same kind (not yet uploaded).
+ * bilu_symbolic (bit for bit), computed on the current device: Algorithm 3's
+ * row merges with one warp per row (rows in ascending order, row i waiting,
+ * bounded, for each pivot row p < i it merges), then the completion of the
+ * pattern -- row pointers (device scans), the L / U' split, the Eq. 4 levels
+ * (a sync-free longest-path pass per triangle, one warp per row) and the
+ * backfill map of Algorithm 5 -- also on the device, straight into the
+ * handle's device copy.  Inputs are host arrays as for bilu_symbolic.  The
+ * returned handle lives on this device; bilu_pattern_upload on the same
+ * device then only builds the schedules.  Its host copy of P' is filled from
+ * the device only when a host-side call needs it (bilu_pattern_export,
+ * bilu_pattern_transpose, bilu_schedule_export, an upload to another device).
  *   row_capacity in [1, 8192]: the most entries any row of P' may hold; a row
  *   that outgrows it returns BILU_ERR_OOM (retry with a larger capacity).
  *   Device scratch of about 8 * n * row_capacity bytes is allocated and freed

@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include <cstring>
+#include <new>
 
 #include "../../include/bilu_tuning.h"
 #include "bilu_internal.h"
@@ -58,10 +59,71 @@ extern "C" const char* bilu_status_string(int status) {
   }
 }
 
+namespace bilu {
+
+DeviceLayout device_layout(int32_t n, int64_t nnz_l, int64_t nnz_u, int64_t nslots) {
+  DeviceLayout d;
+  d.lrp = align256(sizeof(int32_t) * ((size_t)n + 1));
+  d.lci = align256(sizeof(int32_t) * ((size_t)nnz_l + 1));
+  d.urp = d.lrp;
+  d.uci = align256(sizeof(int32_t) * ((size_t)nnz_u + 1));
+  d.map = align256(sizeof(int32_t) * ((size_t)nslots + 1));
+  d.total = d.lrp + d.lci + d.urp + d.uci + d.map;
+  return d;
+}
+
+int ensure_host(const bilu_pattern* cp) {
+  if (cp->host_ready) return BILU_OK;
+  bilu_pattern* p = const_cast<bilu_pattern*>(cp);  // fills the lazily kept host copy (set-up/host calls only)
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) return BILU_ERR_CUDA;
+  if (dev != p->device || !p->d_sym || !p->d_mem) return BILU_ERR_STATE;
+  const size_t n = (size_t)p->n, np = (size_t)p->cnt_p, nl = (size_t)p->cnt_l, nu = (size_t)p->cnt_u;
+  try {
+    p->rp.resize(n + 1);
+    p->ci.resize(np);
+    p->lev.resize(np);
+    p->lvl_l.resize(n);
+    p->lvl_u.resize(n);
+    p->lrp.resize(n + 1);
+    p->urp.resize(n + 1);
+    p->lci.resize(nl);
+    p->uci.resize(nu);
+    p->slot_src.resize((size_t)p->nslots());
+  } catch (const std::bad_alloc&) {
+    return BILU_ERR_OOM;
+  }
+  auto get = [](void* dst, const void* src, size_t count) {
+    return count == 0 || cudaMemcpy(dst, src, count * sizeof(int32_t), cudaMemcpyDeviceToHost) == cudaSuccess;
+  };
+  if (!get(p->rp.data(), p->d_rp, n + 1) || !get(p->ci.data(), p->d_ci, np) || !get(p->lev.data(), p->d_lev, np) ||
+      !get(p->lvl_l.data(), p->d_lvl_l, n) || !get(p->lvl_u.data(), p->d_lvl_u, n) ||
+      !get(p->lrp.data(), p->d_lrp, n + 1) || !get(p->urp.data(), p->d_urp, n + 1) ||
+      !get(p->lci.data(), p->d_lci, nl) || !get(p->uci.data(), p->d_uci, nu) ||
+      !get(p->slot_src.data(), p->d_slot_src, (size_t)p->nslots()))
+    return BILU_ERR_CUDA;
+  p->host_ready = true;
+  return BILU_OK;
+}
+
+}  // namespace bilu
+
 extern "C" int bilu_pattern_upload(bilu_pattern* p, void* stream) {
   if (!p) return BILU_ERR_ARG;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return BILU_ERR_CUDA;
+  if (!p->host_ready && p->d_mem && dev == p->device) {
+    // completed on this device by bilu_symbolic_gpu: the copy is in place
+    if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) return BILU_ERR_CUDA;
+    return build_schedules(p);
+  }
+  if (!p->host_ready) {
+    // completed on another device: bring the host copy back from there first
+    if (cudaSetDevice(p->device) != cudaSuccess) return BILU_ERR_CUDA;
+    const int st = ensure_host(p);
+    cudaSetDevice(dev);
+    if (st != BILU_OK) return st;
+  }
   if (p->d_mem) {
     cudaFree(p->d_mem);
     p->d_mem = nullptr;
@@ -74,22 +136,17 @@ extern "C" int bilu_pattern_upload(bilu_pattern* p, void* stream) {
     p->device = dev;
     return BILU_OK;
   }
-  const size_t s_lrp = align256(sizeof(int32_t) * ((size_t)n + 1));
-  const size_t s_lci = align256(sizeof(int32_t) * (p->lci.size() + 1));
-  const size_t s_urp = s_lrp;
-  const size_t s_uci = align256(sizeof(int32_t) * (p->uci.size() + 1));
-  const size_t s_map = align256(sizeof(int32_t) * (p->slot_src.size() + 1));
-  const size_t total = s_lrp + s_lci + s_urp + s_uci + s_map;
+  const DeviceLayout L = device_layout(n, p->nnz_l(), p->nnz_u(), p->nslots());
   void* mem = nullptr;
-  if (cudaMalloc(&mem, total) != cudaSuccess) {
+  if (cudaMalloc(&mem, L.total) != cudaSuccess) {
     cudaGetLastError();
     return BILU_ERR_OOM;
   }
   char* c = (char*)mem;
-  p->d_lrp = (int32_t*)c; c += s_lrp;
-  p->d_lci = (int32_t*)c; c += s_lci;
-  p->d_urp = (int32_t*)c; c += s_urp;
-  p->d_uci = (int32_t*)c; c += s_uci;
+  p->d_lrp = (int32_t*)c; c += L.lrp;
+  p->d_lci = (int32_t*)c; c += L.lci;
+  p->d_urp = (int32_t*)c; c += L.urp;
+  p->d_uci = (int32_t*)c; c += L.uci;
   p->d_slot_src = (int32_t*)c;
   cudaStream_t s = (cudaStream_t)stream;
   cudaMemcpyAsync(p->d_lrp, p->lrp.data(), sizeof(int32_t) * ((size_t)n + 1), cudaMemcpyHostToDevice, s);
@@ -106,6 +163,11 @@ extern "C" int bilu_pattern_upload(bilu_pattern* p, void* stream) {
   }
   p->d_mem = mem;
   p->device = dev;
+  if (p->d_sym) {  // the device-built copy of P' on the old device is no longer needed
+    cudaFree(p->d_sym);
+    p->d_sym = nullptr;
+    p->d_rp = p->d_ci = p->d_lev = p->d_lvl_l = p->d_lvl_u = nullptr;
+  }
   return build_schedules(p);
 }
 
@@ -128,6 +190,7 @@ extern "C" int bilu_pattern_schedule_info(const bilu_pattern* p, int32_t* solve_
 extern "C" void bilu_destroy_pattern(bilu_pattern* p) {
   if (!p) return;
   if (p->d_mem) cudaFree(p->d_mem);
+  if (p->d_sym) cudaFree(p->d_sym);
   free_schedule(&p->solve);
   free_schedule(&p->fact);
   delete p;
@@ -449,6 +512,8 @@ extern "C" int bilu_schedule_export(const bilu_pattern* p, int32_t rows, int32_t
                                     int32_t* ord_lower, int32_t* ord_upper, int32_t* tick_lower,
                                     int32_t* tick_upper) {
   if (!p || !nchunks || rows < 1 || rows > 1024) return BILU_ERR_ARG;
+  const int st = ensure_host(p);
+  if (st != BILU_OK) return st;
   bilu_chunk_schedule tmp;
   build_schedule(p, rows, true, &tmp);
   *nchunks = tmp.nchunks;

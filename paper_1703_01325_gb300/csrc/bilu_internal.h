@@ -64,9 +64,22 @@ struct bilu_pattern {
   int32_t* d_urp = nullptr;
   int32_t* d_uci = nullptr;
   int32_t* d_slot_src = nullptr;
+  // Sizes of P', L and U' (set by whichever phase built the pattern).
+  int64_t cnt_p = 0, cnt_l = 0, cnt_u = 0;
+  // A pattern completed on the device (bilu_symbolic_gpu) keeps P', the fill
+  // levels and the Eq. 4 levels in device memory (d_sym: rp | ci | lev |
+  // lvl_l | lvl_u) and its host vectors empty until a host-side call needs
+  // them (ensure_host copies them back; no host pass computes them).
+  bool host_ready = true;
+  void* d_sym = nullptr;
+  int32_t* d_rp = nullptr;
+  int32_t* d_ci = nullptr;
+  int32_t* d_lev = nullptr;
+  int32_t* d_lvl_l = nullptr;
+  int32_t* d_lvl_u = nullptr;
 
-  int64_t nnz_l() const { return (int64_t)lci.size(); }
-  int64_t nnz_u() const { return (int64_t)uci.size(); }
+  int64_t nnz_l() const { return cnt_l; }
+  int64_t nnz_u() const { return cnt_u; }
   int64_t nslots() const { return nnz_l() + n + nnz_u(); }
 };
 
@@ -149,6 +162,15 @@ void build_schedule(const bilu_pattern* p, int32_t chunk, bool upper, bilu_chunk
 // Eq. 4 levels, L / U' split and backfill map of a pattern with rp, ci, lev set.
 int complete_pattern(bilu_pattern* p, const int32_t* row_ptr, const int32_t* col_idx);
 int validate_pattern(int32_t n, const int32_t* row_ptr, const int32_t* col_idx);
+// Fills the host vectors of a device-built pattern from its device copies
+// (cudaMemcpy only; the current device must hold them).  Set-up/host calls.
+int ensure_host(const bilu_pattern* p);
+// Layout of a pattern's device copy [lrp | lci | urp | uci | slot_src]
+// (bilu_pattern_upload and bilu_symbolic_gpu build the same one).
+struct DeviceLayout {
+  size_t lrp, lci, urp, uci, map, total;
+};
+DeviceLayout device_layout(int32_t n, int64_t nnz_l, int64_t nnz_u, int64_t nslots);
 void free_schedule(bilu_chunk_schedule* s);
 int launch_apply(const bilu_pattern* p, int32_t b, const double* f, const double* r, double* x,
                  void* work, int32_t* stop, void* stream);

@@ -88,6 +88,9 @@ void finish_pattern(bilu_pattern* p) {
   }
   p->lci.resize((size_t)p->lrp[n]);
   p->uci.resize((size_t)p->urp[n]);
+  p->cnt_p = (int64_t)p->ci.size();
+  p->cnt_l = (int64_t)p->lci.size();
+  p->cnt_u = (int64_t)p->uci.size();
   for (int32_t i = 0; i < n; ++i) {
     int32_t a = p->lrp[i], c = p->urp[i];
     for (int32_t t = p->rp[i]; t < p->rp[i + 1]; ++t) {
@@ -233,6 +236,8 @@ extern "C" int bilu_symbolic(int32_t n, const int32_t* row_ptr, const int32_t* c
 extern "C" int bilu_pattern_transpose(const bilu_pattern* p, bilu_pattern** out) {
   if (!p || !out || p->is_transpose) return BILU_ERR_ARG;
   *out = nullptr;
+  const int st = bilu::ensure_host(p);
+  if (st != BILU_OK) return st;
   bilu_pattern* q = new (std::nothrow) bilu_pattern();
   if (!q) return BILU_ERR_OOM;
   try {
@@ -316,7 +321,7 @@ extern "C" int bilu_pattern_query(const bilu_pattern* p, bilu_pattern_info* info
   info->n = p->n;
   info->k = p->k;
   info->nnz_a = p->nnz_a;
-  info->nnz_p = (int64_t)p->ci.size();
+  info->nnz_p = p->cnt_p;
   info->nnz_l = p->nnz_l();
   info->nnz_u = p->nnz_u();
   info->nlev_l = p->nlev_l;
@@ -327,6 +332,8 @@ extern "C" int bilu_pattern_query(const bilu_pattern* p, bilu_pattern_info* info
 extern "C" int bilu_pattern_export(const bilu_pattern* p, int32_t* row_ptr, int32_t* col_idx,
                                    int32_t* lev, int32_t* lvl_lower, int32_t* lvl_upper) {
   if (!p) return BILU_ERR_ARG;
+  const int st = bilu::ensure_host(p);
+  if (st != BILU_OK) return st;
   const size_t n = (size_t)p->n, nnz = p->ci.size();
   if (row_ptr) std::memcpy(row_ptr, p->rp.data(), sizeof(int32_t) * (n + 1));
   if (col_idx && nnz) std::memcpy(col_idx, p->ci.data(), sizeof(int32_t) * nnz);

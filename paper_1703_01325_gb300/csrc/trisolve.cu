@@ -482,6 +482,7 @@ void free_schedule(bilu_chunk_schedule* s) {
 }
 
 int make_schedule(const bilu_pattern* p, bilu_chunk_schedule* s, int32_t chunk, bool upper) {
+  if (ensure_host(p) != BILU_OK) return (int)cudaErrorInvalidValue;
   bilu_chunk_schedule t;
   build_schedule(p, chunk, upper, &t);
   if (p->n > 0) {

@@ -96,3 +96,29 @@ def test_27pt_ilu2_workload(B):
     the fill structure of the 160 x 160 x 80 27-point ILU(2) case."""
     rp, ci = grid_pattern(64, 64, 32, 27)
     _same(B, 64 * 64 * 32, rp, ci, 2, cap=256, host=False)
+
+
+@pytest.mark.parametrize("grid,stencil,k,b", [((13, 9, 6), 7, 1, 3), ((9, 8, 7), 27, 2, 2), ((40, 1, 1), 7, 0, 4)])
+def test_device_pattern_factor_and_apply(B, grid, stencil, k, b):
+    """A pattern completed on the device (L / U' split, Eq. 4 levels and the
+    backfill map all built there) drives the factorization and the apply to
+    the oracle's results; its upload builds the schedules without copying the
+    structure again."""
+    from paper_1703_01325_gb300.reservoir import reservoir_system
+    from tests.gpu_util import TOL_APPLY, TOL_FACTOR, OracleRun, device_system, rel_maxerr
+    S = reservoir_system(*grid, b, stencil=stencil, sigma=1.0, accum=0.01, seed=17)
+    o = OracleRun(S.n, b, S.row_ptr, S.col_idx, S.vals, k)
+    rp, ci, vals, rhs = device_system(S, "cuda:0")
+    P = B.bilu_symbolic_gpu(S.n, S.row_ptr, S.col_idx, k, row_capacity=256).upload()
+    H = B.bilu_symbolic(S.n, S.row_ptr, S.col_idx, k)
+    assert P.info.nlev_l == H.info.nlev_l and P.info.nlev_u == H.info.nlev_u
+    assert B.bilu_auto_trisolve_chunk(P) == B.bilu_auto_trisolve_chunk(H)
+    assert P.schedule(64)["ord_lower"].tolist() == H.schedule(64)["ord_lower"].tolist()
+    F, info = B.bilu_factor(P, b, vals)
+    assert info.status == 0
+    Lg, Dg, Ug = (t.cpu().numpy() for t in B.factor_sections(P, b, F))
+    assert rel_maxerr(Lg, o.L()) <= TOL_FACTOR
+    assert rel_maxerr(Dg, o.Dinv) <= TOL_FACTOR
+    assert rel_maxerr(Ug, o.U()) <= TOL_FACTOR
+    x = B.bilu_apply(P, b, F, rhs)
+    assert rel_maxerr(x.cpu().numpy(), o.apply(S.rhs)) <= TOL_APPLY
