@@ -70,8 +70,10 @@ int bilu_set_trisolve_warps(int32_t warps);
  *     hands out, a topological order of the chunk dependency graph.  The
  *     lower solve numbers chunks c = 0.. in ascending rows, the upper solve in
  *     descending rows (its chunk c is chunk nchunks - 1 - c above).
- * nchunks is required; any other output may be NULL.  Caller-allocated, host
- * only. */
+ * nchunks is required; any other output may be NULL.  Caller-allocated.  Host
+ * only, except for a pattern bilu_symbolic_gpu left on the device, whose
+ * schedule is built on the current device as bilu_pattern_upload builds it
+ * (the same schedule; synchronises). */
 int bilu_schedule_export(const bilu_pattern* p, int32_t rows, int32_t* nchunks, int32_t* bounds,
                          int32_t* ord_lower, int32_t* ord_upper, int32_t* tick_lower, int32_t* tick_upper);
 

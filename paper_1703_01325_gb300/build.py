@@ -18,7 +18,7 @@ LIB = os.path.join(HERE, "libbilu.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["api.cu", "spmv.cu", "trisolve.cu", "factor.cu", "krylov.cu", "gmres.cu", "adjoint.cu", "profile.cu", "noalloc.cu",
-           "symbolic_gpu.cu", "symbolic.cpp"]
+           "symbolic_gpu.cu", "schedule_gpu.cu", "symbolic.cpp"]
 
 
 def nvcc() -> str:

@@ -512,10 +512,24 @@ extern "C" int bilu_schedule_export(const bilu_pattern* p, int32_t rows, int32_t
                                     int32_t* ord_lower, int32_t* ord_upper, int32_t* tick_lower,
                                     int32_t* tick_upper) {
   if (!p || !nchunks || rows < 1 || rows > 1024) return BILU_ERR_ARG;
-  const int st = ensure_host(p);
-  if (st != BILU_OK) return st;
   bilu_chunk_schedule tmp;
-  build_schedule(p, rows, true, &tmp);
+  if (!p->host_ready) {
+    // a pattern that lives on the device: the device builder, orders copied back
+    const int st = build_schedule_device(p, rows, true, &tmp);
+    if (st != BILU_OK) return st;
+    const size_t n0 = (size_t)p->n;
+    tmp.ord_l.resize(n0);
+    tmp.ord_u.resize(n0);
+    const bool okc = n0 == 0 ||
+                     (cudaMemcpy(tmp.ord_l.data(), tmp.d_ord_l, sizeof(int32_t) * n0, cudaMemcpyDeviceToHost) ==
+                          cudaSuccess &&
+                      cudaMemcpy(tmp.ord_u.data(), tmp.d_ord_u, sizeof(int32_t) * n0, cudaMemcpyDeviceToHost) ==
+                          cudaSuccess);
+    free_schedule(&tmp);
+    if (!okc) return BILU_ERR_CUDA;
+  } else {
+    build_schedule(p, rows, true, &tmp);
+  }
   *nchunks = tmp.nchunks;
   const size_t n = (size_t)p->n;
   auto put = [](int32_t* dst, const std::vector<int32_t>& v) {

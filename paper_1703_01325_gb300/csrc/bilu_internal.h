@@ -159,6 +159,19 @@ size_t apply_workspace_bytes(int32_t n, int32_t b);
 int make_schedule(const bilu_pattern* p, bilu_chunk_schedule* s, int32_t chunk, bool upper);
 // Host part (symbolic.cpp).
 void build_schedule(const bilu_pattern* p, int32_t chunk, bool upper, bilu_chunk_schedule* s);
+// The parts of a schedule both builders share (symbolic.cpp): chunk cuts from
+// the per-row gaps (gapl[r] = r - the last column of L(r), gapu[r] = the first
+// column of U'(r-1) - (r-1), INT32_MAX where there is none), and the claim
+// order by list scheduling over each chunk's distinct predecessors (CSR in
+// solve-order chunk numbers) with priorities prio.
+void schedule_cuts(int32_t n, int32_t target, bool upper, const std::vector<int32_t>& gapl,
+                   const std::vector<int32_t>& gapu, bilu_chunk_schedule* s);
+void ticket_order_lists(int32_t nchunks, const std::vector<int32_t>& prio, const std::vector<int64_t>& pred_ptr,
+                        const std::vector<int32_t>& pred, std::vector<int32_t>& tick);
+// Device part for patterns completed on the device (schedule_gpu.cu): the same
+// schedule as build_schedule, with every pass over P' run on the device; it
+// allocates and fills s->d_mem (ord on the device only).
+int build_schedule_device(const bilu_pattern* p, int32_t chunk, bool upper, bilu_chunk_schedule* s);
 // Eq. 4 levels, L / U' split and backfill map of a pattern with rp, ci, lev set.
 int complete_pattern(bilu_pattern* p, const int32_t* row_ptr, const int32_t* col_idx);
 int validate_pattern(int32_t n, const int32_t* row_ptr, const int32_t* col_idx);

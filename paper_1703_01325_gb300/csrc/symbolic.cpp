@@ -379,12 +379,11 @@ namespace bilu {
 // can start, so chunks are claimed in about the order they can run and few
 // resident CTAs sit on chunks that cannot start yet.  Chunk numbers: lower
 // chunk c is bnd[c]..bnd[c+1]; upper chunk c is lower chunk nchunks-1-c.
-void build_schedule(const bilu_pattern* p, int32_t target, bool upper, bilu_chunk_schedule* s) {
-  const int32_t n = p->n;
-  // chunk boundaries
-  auto gap = [&](int32_t r) -> int64_t {  // 0 < r < n
-    int64_t g = p->lrp[r + 1] > p->lrp[r] ? (int64_t)r - p->lci[p->lrp[r + 1] - 1] : INT64_MAX;
-    if (upper && p->urp[r] > p->urp[r - 1]) g = std::min<int64_t>(g, (int64_t)p->uci[p->urp[r - 1]] - (r - 1));
+void schedule_cuts(int32_t n, int32_t target, bool upper, const std::vector<int32_t>& gapl,
+                   const std::vector<int32_t>& gapu, bilu_chunk_schedule* s) {
+  auto gap = [&](int32_t r) -> int64_t {  // 0 < r < n; INT32_MAX: no dependency that side
+    int64_t g = gapl[(size_t)r];
+    if (upper) g = std::min<int64_t>(g, gapu[(size_t)r]);
     return g;
   };
   s->bnd.clear();
@@ -412,9 +411,55 @@ void build_schedule(const bilu_pattern* p, int32_t target, bool upper, bilu_chun
     s->bnd.push_back(hi);
     lo = hi;
   }
-  const int32_t nchunks = (int32_t)s->bnd.size() - 1;
-  s->nchunks = nchunks;
+  s->nchunks = (int32_t)s->bnd.size() - 1;
   s->max_len = max_len;
+}
+
+void ticket_order_lists(int32_t nchunks, const std::vector<int32_t>& prio, const std::vector<int64_t>& pred_ptr,
+                        const std::vector<int32_t>& pred, std::vector<int32_t>& tick) {
+  // successor lists (CSR by predecessor) and in-degrees from the predecessor lists
+  std::vector<int64_t> off((size_t)nchunks + 1, 0);
+  std::vector<int32_t> indeg((size_t)nchunks, 0);
+  for (int32_t c = 0; c < nchunks; ++c) {
+    indeg[c] = (int32_t)(pred_ptr[(size_t)c + 1] - pred_ptr[c]);
+    for (int64_t e = pred_ptr[c]; e < pred_ptr[(size_t)c + 1]; ++e) ++off[(size_t)pred[e] + 1];
+  }
+  for (int32_t c = 0; c < nchunks; ++c) off[c + 1] += off[c];
+  std::vector<int32_t> succ((size_t)off[nchunks]);
+  {
+    std::vector<int64_t> at(off.begin(), off.end() - 1);
+    for (int32_t c = 0; c < nchunks; ++c)
+      for (int64_t e = pred_ptr[c]; e < pred_ptr[(size_t)c + 1]; ++e) succ[at[pred[e]]++] = c;
+  }
+  std::priority_queue<std::pair<int32_t, int32_t>, std::vector<std::pair<int32_t, int32_t>>,
+                      std::greater<std::pair<int32_t, int32_t>>>
+      ready;
+  for (int32_t c = 0; c < nchunks; ++c)
+    if (indeg[c] == 0) ready.emplace(prio[c], c);
+  tick.clear();
+  tick.reserve((size_t)nchunks);
+  while (!ready.empty()) {
+    const int32_t c = ready.top().second;
+    ready.pop();
+    tick.push_back(c);
+    for (int64_t e = off[c]; e < off[c + 1]; ++e)
+      if (--indeg[succ[e]] == 0) ready.emplace(prio[succ[e]], succ[e]);
+  }
+  // a chunk depends only on chunks earlier in solve order: every chunk is listed
+}
+
+void build_schedule(const bilu_pattern* p, int32_t target, bool upper, bilu_chunk_schedule* s) {
+  const int32_t n = p->n;
+  // chunk boundaries from the gaps: r - (last column of L(r)), and the first
+  // column of U'(r - 1) - (r - 1)
+  std::vector<int32_t> gapl((size_t)n, INT32_MAX), gapu((size_t)n, INT32_MAX);
+  for (int32_t r = 0; r < n; ++r) {
+    if (p->lrp[r + 1] > p->lrp[r]) gapl[r] = r - p->lci[p->lrp[r + 1] - 1];
+    if (r > 0 && p->urp[r] > p->urp[r - 1]) gapu[r] = p->uci[p->urp[r - 1]] - (r - 1);
+  }
+  schedule_cuts(n, target, upper, gapl, gapu, s);
+  const int32_t nchunks = s->nchunks;
+  const int32_t max_len = s->max_len;
   std::vector<int32_t> chunk_of((size_t)n);
   for (int32_t c = 0; c < nchunks; ++c)
     for (int32_t i = s->bnd[c]; i < s->bnd[c + 1]; ++i) chunk_of[i] = c;
@@ -452,8 +497,8 @@ void build_schedule(const bilu_pattern* p, int32_t target, bool upper, bilu_chun
     const std::vector<int32_t>& rpv = up ? p->urp : p->lrp;
     const std::vector<int32_t>& civ = up ? p->uci : p->lci;
     const std::vector<int32_t>& lvl = up ? p->lvl_u : p->lvl_l;
-    std::vector<int32_t> prio((size_t)nchunks, 0), indeg((size_t)nchunks, 0), seen((size_t)nchunks, -1);
-    std::vector<int32_t> epred, esucc;  // distinct edges pred -> succ (solve-order chunk numbers)
+    std::vector<int32_t> prio((size_t)nchunks, 0), seen((size_t)nchunks, -1), pred;
+    std::vector<int64_t> pred_ptr((size_t)nchunks + 1, 0);  // distinct predecessors (solve-order numbers)
     for (int32_t c = 0; c < nchunks; ++c) {
       const int32_t lc = up ? nchunks - 1 - c : c;  // the chunk's rows
       const int32_t lo = s->bnd[lc], hi = s->bnd[lc + 1];
@@ -466,37 +511,13 @@ void build_schedule(const bilu_pattern* p, int32_t target, bool upper, bilu_chun
           const int32_t cj = up ? nchunks - 1 - chunk_of[j] : chunk_of[j];
           if (seen[cj] == c) continue;
           seen[cj] = c;
-          epred.push_back(cj);
-          esucc.push_back(c);
-          ++indeg[c];
+          pred.push_back(cj);
         }
       }
       prio[c] = pm;
+      pred_ptr[(size_t)c + 1] = (int64_t)pred.size();
     }
-    // successor lists in CSR form
-    std::vector<int64_t> off((size_t)nchunks + 1, 0);
-    for (int32_t e : epred) ++off[(size_t)e + 1];
-    for (int32_t c = 0; c < nchunks; ++c) off[c + 1] += off[c];
-    std::vector<int32_t> succ(epred.size());
-    {
-      std::vector<int64_t> at(off.begin(), off.end() - 1);
-      for (size_t e = 0; e < epred.size(); ++e) succ[at[epred[e]]++] = esucc[e];
-    }
-    std::priority_queue<std::pair<int32_t, int32_t>, std::vector<std::pair<int32_t, int32_t>>,
-                        std::greater<std::pair<int32_t, int32_t>>>
-        ready;
-    for (int32_t c = 0; c < nchunks; ++c)
-      if (indeg[c] == 0) ready.emplace(prio[c], c);
-    tick.clear();
-    tick.reserve((size_t)nchunks);
-    while (!ready.empty()) {
-      const int32_t c = ready.top().second;
-      ready.pop();
-      tick.push_back(c);
-      for (int64_t e = off[c]; e < off[c + 1]; ++e)
-        if (--indeg[succ[e]] == 0) ready.emplace(prio[succ[e]], succ[e]);
-    }
-    // a chunk depends only on chunks earlier in solve order: every chunk is listed
+    ticket_order_lists(nchunks, prio, pred_ptr, pred, tick);
   };
   ticket_order(false, s->tick_l);
   if (upper) ticket_order(true, s->tick_u);

@@ -482,8 +482,15 @@ void free_schedule(bilu_chunk_schedule* s) {
 }
 
 int make_schedule(const bilu_pattern* p, bilu_chunk_schedule* s, int32_t chunk, bool upper) {
-  if (ensure_host(p) != BILU_OK) return (int)cudaErrorInvalidValue;
   bilu_chunk_schedule t;
+  if (!p->host_ready) {
+    // completed on the device: every pass over P' on the device too
+    const int st = build_schedule_device(p, chunk, upper, &t);
+    if (st != BILU_OK) return (int)cudaErrorMemoryAllocation;
+    free_schedule(s);
+    *s = std::move(t);
+    return 0;
+  }
   build_schedule(p, chunk, upper, &t);
   if (p->n > 0) {
     const size_t one = align256(sizeof(int32_t) * (size_t)p->n);

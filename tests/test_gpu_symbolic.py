@@ -122,3 +122,32 @@ def test_device_pattern_factor_and_apply(B, grid, stencil, k, b):
     assert rel_maxerr(Ug, o.U()) <= TOL_FACTOR
     x = B.bilu_apply(P, b, F, rhs)
     assert rel_maxerr(x.cpu().numpy(), o.apply(S.rhs)) <= TOL_APPLY
+
+
+@pytest.mark.parametrize("grid,stencil,k,rows", [((16, 16, 8), 7, 1, 32), ((33, 9, 6), 27, 2, 64),
+                                                 ((128, 128, 64), 7, 1, 256), ((24, 20, 10), 7, 0, 1024)])
+def test_device_schedule_equals_host_schedule(B, grid, stencil, k, rows):
+    """The schedule built for a pattern that lives on the device (per-row gaps,
+    each chunk's local-level order, the chunk priorities and the predecessor
+    lists on the device; cuts and list scheduling on the host from those) is
+    the host builder's, bit for bit: chunk bounds, both row orders, both claim
+    orders."""
+    rp, ci = grid_pattern(*grid, stencil)
+    n = int(np.prod(grid))
+    g = B.bilu_symbolic_gpu(n, rp, ci, k, row_capacity=256).schedule(rows)
+    h = B.bilu_symbolic(n, rp, ci, k).schedule(rows)
+    for key in ("bounds", "ord_lower", "ord_upper", "tick_lower", "tick_upper"):
+        assert np.array_equal(g[key], h[key]), key
+
+
+def test_random_pattern_device_schedule(B):
+    """Irregular patterns: many predecessor chunks per chunk."""
+    for seed in range(3):
+        n = 700 + 50 * seed
+        rp, ci = random_pattern(n, density=0.006 + 0.002 * seed, seed=900 + seed, symmetric=seed == 1)
+        for k in (0, 2):
+            for rows in (7, 64):
+                g = B.bilu_symbolic_gpu(n, rp, ci, k, row_capacity=n).schedule(rows)
+                h = B.bilu_symbolic(n, rp, ci, k).schedule(rows)
+                for key in ("bounds", "ord_lower", "ord_upper", "tick_lower", "tick_upper"):
+                    assert np.array_equal(g[key], h[key]), (seed, k, rows, key)
