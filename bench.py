@@ -532,15 +532,36 @@ def fp32_kernel_rates(B, S, P, F, vals, rhs, rp, ci, dev, stream, reps=10):
     return res
 
 
+def _oracle_ref_job(job):
+    """Worker of the sweep's process pool (spawned, so it holds no CUDA
+    context): the oracle's FP64 solution of one generated system."""
+    wl, b, k = job
+    from paper_1703_01325_gb300.reservoir import WORKLOADS, reservoir_system
+    cfg = dict(WORKLOADS[wl])
+    cfg["b"] = b
+    ref = oracle_solution(reservoir_system(**cfg), k, tol=1e-10, maxit=2000)
+    return job, ref
+
+
 def sweep(B, dev, stream, which, tol=1e-8, reps=20, with_oracle=False):
-    """Per-configuration numbers, one JSON line each: the device symbolic
-    phase, FP64 and FP32 factorization, FP64 and FP32 apply and SpMV (mean
-    CUDA-event time over `reps` calls, algorithmic GB/s), and BiCGSTAB from
-    x0 = 0 to a true relative residual of `tol` with the FP64 preconditioner
-    and with the FP32-stored one (median of `solve_reps` solves, factorization
-    excluded).  Inputs are larger than L2 in every configuration.  The
-    160 x 160 x 80 case reaches 1e-8 in neither precision: its solves run a
-    300-iteration budget once and report where they stand."""
+    """Per-configuration numbers, one JSON line each: the device set-up
+    (symbolic phase and schedules, bilu_symbolic_gpu + bilu_pattern_upload),
+    FP64 and FP32 factorization, FP64 and FP32 apply and SpMV (mean CUDA-event
+    time over `reps` calls, algorithmic GB/s), and the solvers from x0 = 0
+    toward a true relative residual of `tol`.
+
+    c2 (96 x 96 x 48, b in {2,4,6,8}, k in {0,1,2}): BiCGSTAB with the FP64
+    preconditioner and with the FP32-stored one (median of 3 solves,
+    factorization excluded); with `with_oracle`, each solution's error against
+    the CPU oracle's FP64 solution (computed by a pool of spawned processes on
+    the host cores while the GPU sweeps) and the oracle's kernel times.
+
+    c3 (160 x 160 x 80 27-point ILU(2)): no solver reaches 1e-8, so the four
+    solvers get the same budget of work and report where they stand: FP64
+    BiCGSTAB and FP32-preconditioned BiCGSTAB with 300 iterations (two applies
+    and two SpMVs each), FP64 refinement around FP32 BiCGSTAB with 300 inner
+    iterations, GMRES(20) with 600 Arnoldi steps (one apply and one SpMV
+    each); also the host symbolic phase for comparison with the device one."""
     import torch
     from paper_1703_01325_gb300.reservoir import WORKLOADS, reservoir_system
     if which == "c2":
@@ -550,6 +571,11 @@ def sweep(B, dev, stream, which, tol=1e-8, reps=20, with_oracle=False):
         cases = [("grid160x160x80_27pt_b3", 3, 2)]
         maxit, solve_reps = 300, 1
     hbm, _ = peaks()
+    pool = refs = None
+    if with_oracle and which == "c2":
+        import multiprocessing as mp
+        pool = mp.get_context("spawn").Pool(min(len(cases), os.cpu_count() or 1))
+        refs = pool.map_async(_oracle_ref_job, cases)
 
     def timed(fn, n):
         fn()
@@ -562,14 +588,27 @@ def sweep(B, dev, stream, which, tol=1e-8, reps=20, with_oracle=False):
         torch.cuda.synchronize()
         return e0.elapsed_time(e1) / n
 
+    def timed_solve(fn):
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        si = fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return {"ms": round(e0.elapsed_time(e1), 2), "iters": si.iters, "true_relres": si.true_relres,
+                "status": si.status}
+
+    rows, xs = [], {}
     for wl, b, k in cases:
         cfg = dict(WORKLOADS[wl])
         cfg["b"] = b
         S = reservoir_system(**cfg)
+        torch.cuda.synchronize()
         t0 = time.perf_counter()
         P = B.bilu_symbolic_gpu(S.n, S.row_ptr, S.col_idx, k)
-        sym_ms = (time.perf_counter() - t0) * 1e3
+        t1 = time.perf_counter()
         P.upload()
+        t2 = time.perf_counter()
         info = P.info
         rp, ci = torch.from_numpy(S.row_ptr).to(dev), torch.from_numpy(S.col_idx).to(dev)
         vals, rhs = torch.from_numpy(S.vals.reshape(-1)).to(dev), torch.from_numpy(S.rhs).to(dev)
@@ -582,7 +621,9 @@ def sweep(B, dev, stream, which, tol=1e-8, reps=20, with_oracle=False):
         V32 = B.bilu_convert_f32(vals)
         x, y = torch.empty_like(rhs), torch.empty_like(rhs)
         row = {"workload": wl, "b": b, "k": k, "n": S.n, "nnzb": S.nnzb, "nnz_l": info.nnz_l,
-               "nnz_u": info.nnz_u, "levels_lower": info.nlev_l, "symbolic_gpu_ms": round(sym_ms, 1)}
+               "nnz_u": info.nnz_u, "levels_lower": info.nlev_l,
+               "setup_ms": {"symbolic_gpu": round((t1 - t0) * 1e3, 1), "schedules_upload": round((t2 - t1) * 1e3, 1),
+                            "total": round((t2 - t0) * 1e3, 1)}}
         row["factor_ms"] = round(timed(lambda: B.bilu_factor(P, b, vals, F, fw), 3), 2)
         row["factor_f32_ms"] = round(timed(lambda: B.bilu_factor_f32(P, b, vals, F32, fw), 3), 2)
         B.bilu_factor(P, b, vals, F, fw)
@@ -599,29 +640,62 @@ def sweep(B, dev, stream, which, tol=1e-8, reps=20, with_oracle=False):
                 ms = timed(fn, reps)
                 gbs = by / (ms * 1e-3) / 1e9
                 row[f"{name}_{tag}"] = {"us": round(ms * 1e3, 1), "gbs": round(gbs, 1), "frac_hbm": round(gbs / hbm, 3)}
-        for tag, fac in (("bicgstab_f64", None), ("bicgstab_f32prec", F32)):
-            runs = []
-            for _ in range(solve_reps):
-                x.zero_()
-                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                torch.cuda.synchronize()
-                e0.record(stream)
-                if fac is None:
-                    si = B.bicgstab_solve(P, A, F, rhs, x=x, tol=tol, maxit=maxit, work=sw)[1]
-                else:
-                    si = B.bicgstab_solve_f32prec(P, A, F32, rhs, x=x, tol=tol, maxit=maxit, work=sw)[1]
-                e1.record(stream)
-                torch.cuda.synchronize()
-                runs.append((e0.elapsed_time(e1), si))
-            runs.sort(key=lambda r: r[0])
-            ms, si = runs[len(runs) // 2]
-            row[tag] = {"ms": round(ms, 2), "iters": si.iters, "true_relres": si.true_relres, "status": si.status}
-        if with_oracle and which == "c2":
-            row["cpu_baseline"] = oracle_kernel_times(S, k)
-        print(json.dumps(row), flush=True)
+        if which == "c2":
+            for tag, fac in (("bicgstab_f64", None), ("bicgstab_f32prec", F32)):
+                runs = []
+                for _ in range(solve_reps):
+                    x.zero_()
+                    if fac is None:
+                        r = timed_solve(lambda: B.bicgstab_solve(P, A, F, rhs, x=x, tol=tol, maxit=maxit, work=sw)[1])
+                    else:
+                        r = timed_solve(lambda: B.bicgstab_solve_f32prec(P, A, F32, rhs, x=x, tol=tol, maxit=maxit,
+                                                                         work=sw)[1])
+                    runs.append(r)
+                runs.sort(key=lambda r: r["ms"])
+                row[tag] = runs[len(runs) // 2]
+                xs[(b, k, tag)] = x.cpu().numpy()
+            if with_oracle:
+                row["cpu_baseline"] = oracle_kernel_times(S, k)
+        else:
+            mw = B.workspace(P.bicgstab_mixed_workspace_bytes(b), dev)
+            gw = B.workspace(int(B.L.load().gmres_workspace_bytes(P.handle, b, 20)), dev)
+            x.zero_()
+            row["bicgstab_f64"] = timed_solve(lambda: B.bicgstab_solve(P, A, F, rhs, x=x, tol=tol, maxit=300,
+                                                                       work=sw)[1])
+            x.zero_()
+            row["bicgstab_f32prec"] = timed_solve(lambda: B.bicgstab_solve_f32prec(P, A, F32, rhs, x=x, tol=tol,
+                                                                                   maxit=300, work=sw)[1])
+            x.zero_()
+            row["mixed_refinement"] = timed_solve(lambda: B.bicgstab_solve_mixed(
+                P, A, V32, F32, rhs, x=x, tol=tol, maxit=300, inner_tol=1e-3, inner_maxit=100, work=mw)[1])
+            x.zero_()
+            row["gmres20_f64"] = timed_solve(lambda: B.gmres_solve(P, A, F, rhs, x=x, tol=tol, maxit=600, restart=20,
+                                                                   work=gw)[1])
+            row["budget"] = ("equal work: 300 BiCGSTAB iterations (2 applies + 2 SpMVs each), 300 inner iterations of "
+                             "the refinement, 600 GMRES(20) steps (1 apply + 1 SpMV each)")
+            t3 = time.perf_counter()
+            H = B.bilu_symbolic(S.n, S.row_ptr, S.col_idx, k)
+            row["setup_ms"]["symbolic_host_for_comparison"] = round((time.perf_counter() - t3) * 1e3, 1)
+            H.close()
+            del mw, gw
+        rows.append(row)
+        if refs is None:
+            print(json.dumps(row), flush=True)
         del F, F32, fw, aw, sw, V32, vals
         P.close()
         torch.cuda.empty_cache()
+    if refs is not None:
+        import numpy as np
+        done = dict(refs.get())
+        pool.close()
+        pool.join()
+        for row in rows:
+            ref = done[("grid96x96x48_7pt", row["b"], row["k"])]
+            for tag in ("bicgstab_f64", "bicgstab_f32prec"):
+                xv = xs[(row["b"], row["k"], tag)]
+                row[tag]["x_rel_err_vs_oracle"] = float(np.linalg.norm(xv - ref["x"]) / np.linalg.norm(ref["x"]))
+            row["oracle_reference"] = {k2: ref[k2] for k2 in ("iters", "true_relres", "status", "seconds")}
+            print(json.dumps(row), flush=True)
 
 
 def main():

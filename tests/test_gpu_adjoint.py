@@ -219,3 +219,48 @@ def test_autograd_matches_plain_finite_differences_small(B):
     already agrees to 1e-5 on a well-conditioned small system."""
     S = reservoir_system(8, 8, 8, 3, sigma=1.0, accum=0.1, seed=17)
     _fd_check(B, S, 1, 16, 1e-5, stable=False)
+
+
+def test_autograd_matches_plain_central_differences_64x64x32(B):
+    """64 x 64 x 32 cells, b = 3, ILU(1): plain central differences (h = 1e-6)
+    of L = ||W x||^2 on 32 entries (16 block values, 16 right-hand side
+    components) -- two independent evaluations L(+h) and L(-h), subtracted --
+    against the adjoint gradient, entry by entry:
+    |fd - g_q| <= 1e-5 * max(|g_q|, 1e-3 max|g|).  Each perturbed system is
+    solved to 1e-13 by one refinement step from the unperturbed solution x0
+    (x = x0 + d, A(+-h) d = rhs(+-h) - A(+-h) x0), so the solver's error in x0
+    is common to both evaluations instead of swamping their O(h) difference."""
+    from paper_1703_01325_gb300.adjoint import BlockILUSolver
+    S = reservoir_system(64, 64, 32, 3, sigma=1.0, accum=0.01, seed=1703)
+    b = S.b
+    w = torch.from_numpy(loss_weights(S.n, b, seed=1703)).to(DEV)
+    solver = BlockILUSolver(S.n, b, S.row_ptr, S.col_idx, 1, tol=1e-13, device=DEV)
+    vals0 = torch.from_numpy(S.vals.reshape(-1).copy()).to(DEV)
+    rhs0 = torch.from_numpy(S.rhs.copy()).to(DEV)
+    vals = vals0.clone().requires_grad_(True)
+    rhs = rhs0.clone().requires_grad_(True)
+    ((w * solver.solve(vals, rhs)) ** 2).sum().backward()
+    gv, gr = vals.grad.cpu().numpy(), rhs.grad.cpu().numpy()
+    rp, ci = (torch.from_numpy(a).to(DEV) for a in (S.row_ptr, S.col_idx))
+    with torch.no_grad():
+        x0 = solver.solve(vals0, rhs0).detach()
+
+        def loss(v, r):
+            d = solver.solve(v, r - B.bsr_spmv(S.n, b, rp, ci, v, x0)).detach()
+            return float(((w * (x0 + d)) ** 2).sum())
+
+        rng = np.random.default_rng(32)
+        h = 1e-6
+        for which, g, base in (("vals", gv, vals0), ("rhs", gr, rhs0)):
+            idx = rng.choice(base.numel(), 16, replace=False)
+            gmax = np.abs(g).max()
+            for q in idx:
+                p, m = base.clone(), base.clone()
+                p[q] += h
+                m[q] -= h
+                if which == "vals":
+                    fd = (loss(p, rhs0) - loss(m, rhs0)) / (2 * h)
+                else:
+                    fd = (loss(vals0, p) - loss(vals0, m)) / (2 * h)
+                bound = 1e-5 * max(abs(g[q]), 1e-3 * gmax)
+                assert abs(fd - g[q]) <= bound, (which, int(q), fd, g[q], bound)
