@@ -79,6 +79,10 @@ def parse():
                     help="with --sweep c2: add the CPU oracle's kernel times (one call each, one thread)")
     ap.add_argument("--no-extras", action="store_true",
                     help="time the step only (no small-case, FP32-kernel or precision sections)")
+    ap.add_argument("--kernel-case", choices=["apply", "apply_f32", "spmv", "spmv_f32", "spmv_f32x"], default=None,
+                    help="instead of the bench line: run one preconditioner apply or SpMV --reps times on "
+                         "--workload (the small single-kernel case for profilers)")
+    ap.add_argument("--reps", type=int, default=3)
     return ap.parse_args()
 
 
@@ -506,7 +510,9 @@ def precision_compare(B, dev, stream, cases=((2, 1), (4, 1)), tol=1e-8, with_ora
 
 def fp32_kernel_rates(B, S, P, F, vals, rhs, rp, ci, dev, stream, reps=10):
     """FP32-stored apply and FP32 SpMV on the main workload: mean CUDA-event
-    time and algorithmic GB/s (4-byte values)."""
+    time and algorithmic GB/s (4-byte values).  spmv_f32 reads x in FP64,
+    spmv_f32x in FP32 (the SpMV of the mixed solve, on the FP32 apply's
+    result)."""
     import torch
     info = P.info
     b = S.b
@@ -516,8 +522,11 @@ def fp32_kernel_rates(B, S, P, F, vals, rhs, rp, ci, dev, stream, reps=10):
     aw = B.workspace(P.apply_workspace_bytes(b), dev)
     x, y = torch.empty_like(rhs), torch.empty_like(rhs)
     res = {}
+    x32 = rhs.float()
     for name, fn, by in (("apply_f32", lambda: B.bilu_apply_f32(P, b, F32, rhs, x, aw), ab["apply"]),
-                         ("spmv_f32", lambda: B.bsr_spmv_f32(S.n, b, rp, ci, V32, rhs, y), ab["spmv"])):
+                         ("spmv_f32", lambda: B.bsr_spmv_f32(S.n, b, rp, ci, V32, rhs, y), ab["spmv"]),
+                         ("spmv_f32x", lambda: B.bsr_spmv_f32x(S.n, b, rp, ci, V32, x32, y),
+                          ab["spmv"] - 4 * S.n * b)):
         for _ in range(3):
             fn()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -636,7 +645,12 @@ def sweep(B, dev, stream, which, tol=1e-8, reps=20, with_oracle=False):
             else:
                 fa = lambda: B.bilu_apply_f32(P, b, F32, rhs, x, aw)
                 fs = lambda: B.bsr_spmv_f32(S.n, b, rp, ci, V32, rhs, y)
-            for name, fn, by in (("apply", fa, ab["apply"]), ("spmv", fs, ab["spmv"])):
+            kerns = [("apply", fa, ab["apply"]), ("spmv", fs, ab["spmv"])]
+            if tag == "f32":  # the mixed solve's SpMV: x in FP32, as the FP32 apply leaves it
+                x32 = rhs.float()
+                kerns.append(("spmv_x32", lambda: B.bsr_spmv_f32x(S.n, b, rp, ci, V32, x32, y),
+                              ab["spmv"] - 4 * S.n * b))
+            for name, fn, by in kerns:
                 ms = timed(fn, reps)
                 gbs = by / (ms * 1e-3) / 1e9
                 row[f"{name}_{tag}"] = {"us": round(ms * 1e3, 1), "gbs": round(gbs, 1), "frac_hbm": round(gbs / hbm, 3)}
@@ -698,10 +712,49 @@ def sweep(B, dev, stream, which, tol=1e-8, reps=20, with_oracle=False):
             print(json.dumps(row), flush=True)
 
 
+def kernel_case(args):
+    """One kernel family on one workload, args.reps launches after set-up, and
+    a one-line status: the target of single-kernel profiler captures."""
+    import torch
+    import paper_1703_01325_gb300.bilu as B
+    dev = torch.device("cuda:0")
+    torch.cuda.set_device(dev)
+    S, _ = system(args)
+    b = S.b
+    P = B.bilu_symbolic(S.n, S.row_ptr, S.col_idx, args.k).upload()
+    rp, ci = torch.from_numpy(S.row_ptr).to(dev), torch.from_numpy(S.col_idx).to(dev)
+    vals, rhs = torch.from_numpy(S.vals.reshape(-1)).to(dev), torch.from_numpy(S.rhs).to(dev)
+    F, _ = B.bilu_factor(P, b, vals)
+    aw = B.workspace(P.apply_workspace_bytes(b), dev)
+    x = torch.empty_like(rhs)
+    if args.kernel_case == "apply":
+        fn = lambda: B.bilu_apply(P, b, F, rhs, x, aw)
+    elif args.kernel_case == "apply_f32":
+        F32 = B.bilu_convert_f32(F)
+        fn = lambda: B.bilu_apply_f32(P, b, F32, rhs, x, aw)
+    elif args.kernel_case == "spmv":
+        fn = lambda: B.bsr_spmv(S.n, b, rp, ci, vals, rhs, x)
+    elif args.kernel_case == "spmv_f32":
+        V32 = B.bilu_convert_f32(vals)
+        fn = lambda: B.bsr_spmv_f32(S.n, b, rp, ci, V32, rhs, x)
+    else:
+        V32, x32 = B.bilu_convert_f32(vals), rhs.float()
+        fn = lambda: B.bsr_spmv_f32x(S.n, b, rp, ci, V32, x32, x)
+    for _ in range(args.reps):
+        fn()
+    torch.cuda.synchronize()
+    print(json.dumps({"kernel_case": args.kernel_case, "workload": args.workload, "b": b, "k": args.k,
+                      "reps": args.reps, "workspace_status": B.bilu_workspace_status(aw)}))
+    P.close()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.kernel_case:
+        kernel_case(args)
         return
     if args.sweep:
         import torch

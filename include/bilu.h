@@ -355,10 +355,18 @@ int bilu_convert_f32(const double* d_src, float* d_dst, int64_t count, void* str
 int bilu_apply_f32(const bilu_pattern* p, int32_t b, const float* d_factors32, const double* d_r,
                    double* d_x, void* d_work, size_t work_bytes, void* stream);
 
-/* y = A x with A's values in FP32 (FP32 products and sums; x read and y
- * written in FP64).  Asynchronous. */
+/* y = A x with A's values in FP32 (FP32 products and sums, each block row
+ * summed over its blocks in column order; x read and y written in FP64, x
+ * rounded to FP32 to nearest).  Asynchronous. */
 int bsr_spmv_f32(int32_t n, int32_t b, const int32_t* d_row_ptr, const int32_t* d_col_idx,
                  const float* d_vals32, const double* d_x, double* d_y, void* stream);
+
+/* y = A x with A's values and x in FP32 (d_x32: device, n*b floats; y in
+ * FP64): the products and sums of bsr_spmv_f32, so its y for x equals this
+ * call's y for x rounded to FP32.  bicgstab_solve_mixed uses it on the FP32
+ * preconditioner's own FP32 result.  Asynchronous. */
+int bsr_spmv_f32x(int32_t n, int32_t b, const int32_t* d_row_ptr, const int32_t* d_col_idx,
+                  const float* d_vals32, const float* d_x32, double* d_y, void* stream);
 
 /* Scratch bytes bicgstab_solve_mixed needs. */
 size_t bicgstab_mixed_workspace_bytes(const bilu_pattern* p, int32_t b);

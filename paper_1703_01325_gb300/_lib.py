@@ -72,6 +72,7 @@ SIGNATURES = {
     "bilu_convert_f32": (C.c_int, [_vp, _vp, C.c_int64, _vp]),
     "bilu_apply_f32": (C.c_int, [_vp, C.c_int32, _vp, _vp, _vp, _vp, C.c_size_t, _vp]),
     "bsr_spmv_f32": (C.c_int, [C.c_int32, C.c_int32, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "bsr_spmv_f32x": (C.c_int, [C.c_int32, C.c_int32, _vp, _vp, _vp, _vp, _vp, _vp]),
     "bicgstab_mixed_workspace_bytes": (C.c_size_t, [_vp, C.c_int32]),
     "bicgstab_solve_mixed": (C.c_int, [_vp, C.POINTER(BSR), _vp, _vp, _vp, _vp, C.c_double, C.c_int32,
                                        C.c_double, C.c_int32, _vp, C.c_size_t, _vp, C.POINTER(SolveInfo)]),

@@ -386,6 +386,18 @@ def bsr_spmv_f32(n: int, b: int, row_ptr: torch.Tensor, col_idx: torch.Tensor, v
     return y
 
 
+def bsr_spmv_f32x(n: int, b: int, row_ptr: torch.Tensor, col_idx: torch.Tensor, vals32: torch.Tensor,
+                  x32: torch.Tensor, y: torch.Tensor | None = None, stream=None):
+    """y = A x with A's values and x in FP32 (FP32 arithmetic, y in FP64)."""
+    if y is None:
+        y = torch.empty(x32.shape, dtype=torch.float64, device=x32.device)
+    _check(L.load().bsr_spmv_f32x(n, b, _dev(row_ptr, torch.int32, "row_ptr"),
+                                  _dev(col_idx, torch.int32, "col_idx"), _dev(vals32, torch.float32, "vals32"),
+                                  _dev(x32, torch.float32, "x32"), _dev(y, torch.float64, "y"),
+                                  _stream_handle(stream)), "bsr_spmv_f32x")
+    return y
+
+
 def bicgstab_solve_mixed(pattern: Pattern, A, vals32: torch.Tensor, factors32: torch.Tensor,
                          rhs: torch.Tensor, x: torch.Tensor | None = None, tol: float = 1e-8,
                          maxit: int = 1000, inner_tol: float = 1e-4, inner_maxit: int = 200,

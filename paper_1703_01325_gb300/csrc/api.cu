@@ -426,6 +426,15 @@ extern "C" int bsr_spmv_f32(int32_t n, int32_t b, const int32_t* d_row_ptr, cons
   return cuda_status(launch_spmv_f32(n, b, d_row_ptr, d_col_idx, d_vals32, d_x, d_y, stream));
 }
 
+extern "C" int bsr_spmv_f32x(int32_t n, int32_t b, const int32_t* d_row_ptr, const int32_t* d_col_idx,
+                             const float* d_vals32, const float* d_x32, double* d_y, void* stream) {
+  if (n < 0 || !valid_b(b)) return BILU_ERR_ARG;
+  if (n == 0) return BILU_OK;
+  if (!d_row_ptr || !d_col_idx || !d_vals32 || !d_x32 || !d_y || (const void*)d_x32 == (const void*)d_y)
+    return BILU_ERR_ARG;
+  return cuda_status(launch_spmv_f32x(n, b, d_row_ptr, d_col_idx, d_vals32, d_x32, d_y, stream));
+}
+
 extern "C" size_t bicgstab_mixed_workspace_bytes(const bilu_pattern* p, int32_t b) {
   if (!p || !valid_b(b)) return 0;
   return krylov_mixed_workspace_bytes(p->n, b);

@@ -141,6 +141,11 @@ int launch_spmv(int32_t n, int32_t b, const int32_t* rp, const int32_t* ci, cons
                 const double* x, double* y, void* stream, const int32_t* stop = nullptr);
 int launch_spmv_f32(int32_t n, int32_t b, const int32_t* rp, const int32_t* ci, const float* vals,
                     const double* x, double* y, void* stream, const int32_t* stop = nullptr);
+int launch_spmv_f32x(int32_t n, int32_t b, const int32_t* rp, const int32_t* ci, const float* vals,
+                     const float* x, double* y, void* stream, const int32_t* stop = nullptr);
+// The FP32 apply's result in FP32 (the vector the FP32 apply widens into its
+// FP64 output), inside its workspace.
+const float* apply_f32_result(const void* work, int32_t n, int32_t b);
 int launch_convert_f32(const double* src, float* dst, long long count, void* stream,
                        const int32_t* stop = nullptr);
 
@@ -196,9 +201,12 @@ int launch_apply_f32(const bilu_pattern* p, int32_t b, const float* f, const dou
 
 // The operators a BiCGSTAB run uses: y = A x and z = M^{-1} r, both gated by
 // the device stop word (nullptr: always run); `work` is the apply workspace.
+// spmv_applied (optional, else spmv) is the SpMV of the vector the last
+// apply call produced, which may read the apply's own copy of it in `work`.
 struct KOps {
   std::function<int(const double*, double*, int32_t*, void*)> spmv;
   std::function<int(const double*, double*, int32_t*, void*)> apply;
+  std::function<int(const double*, double*, int32_t*, void*)> spmv_applied;
 };
 
 size_t krylov_workspace_bytes(int32_t n, int32_t b);

@@ -331,6 +331,7 @@ int bicgstab_core(const KOps& ops, long long m, const double* rhs, double* x, do
   int32_t* aheader = reinterpret_cast<int32_t*>(awork);
   int32_t* stop = &st->stop;
   const int vb = kRedBlocks, vt = kRedThreads;
+  const auto& spmv_applied = ops.spmv_applied ? ops.spmv_applied : ops.spmv;
 
   cudaMemsetAsync(aheader, 0, kHeaderBytes, s);
   int status = BILU_OK;
@@ -346,13 +347,13 @@ int bicgstab_core(const KOps& ops, long long m, const double* rhs, double* x, do
       for (int it = 0; it < batch; ++it) {
         { ProfScope ps_(BILU_PROF_KRYLOV, s); k_update_p<<<vb, vt, 0, s>>>(m, st, r, pv, v); }
         ops.apply(pv, ph, stop, awork);
-        ops.spmv(ph, v, stop, awork);
+        spmv_applied(ph, v, stop, awork);
         { ProfScope ps_(BILU_PROF_KRYLOV, s); k_dot<<<vb, vt, 0, s>>>(m, st, rh, v, partials); }
         { ProfScope ps_(BILU_PROF_KRYLOV, s); k_fin<<<1, vt, 0, s>>>(st, partials, kFinAlpha, 1, tol); }
         { ProfScope ps_(BILU_PROF_KRYLOV, s); k_s<<<vb, vt, 0, s>>>(m, st, r, v, ph, sv, x, partials); }
         { ProfScope ps_(BILU_PROF_KRYLOV, s); k_fin<<<1, vt, 0, s>>>(st, partials, kFinS, 1, tol); }
         ops.apply(sv, sh, stop, awork);
-        ops.spmv(sh, t, stop, awork);
+        spmv_applied(sh, t, stop, awork);
         { ProfScope ps_(BILU_PROF_KRYLOV, s); k_dot_ts<<<vb, vt, 0, s>>>(m, st, t, sv, partials); }
         { ProfScope ps_(BILU_PROF_KRYLOV, s); k_fin<<<1, vt, 0, s>>>(st, partials, kFinOmega, 2, tol); }
         { ProfScope ps_(BILU_PROF_KRYLOV, s); k_xr<<<vb, vt, 0, s>>>(m, st, sh, sv, t, rh, x, r, partials); }
@@ -480,6 +481,12 @@ int run_bicgstab_mixed(const bilu_pattern* p, const bilu_bsr* A, const float* va
   KOps ops;
   ops.spmv = [=](const double* xin, double* yout, int32_t* stop, void*) {
     return launch_spmv_f32(n, b, A->row_ptr, A->col_idx, vals32, xin, yout, stream, stop);
+  };
+  // p_hat and s_hat come from the FP32 apply: its FP32 result is x rounded to
+  // FP32 exactly, so the SpMV reads that (the same products and sums)
+  ops.spmv_applied = [=](const double*, double* yout, int32_t* stop, void* aw) {
+    return launch_spmv_f32x(n, b, A->row_ptr, A->col_idx, vals32, apply_f32_result(aw, n, b), yout, stream,
+                            stop);
   };
   ops.apply = [=](const double* rin, double* zout, int32_t* stop, void* aw) {
     return launch_apply_f32(p, b, f32, rin, zout, aw, stop, stream);

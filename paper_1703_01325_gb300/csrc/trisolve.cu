@@ -474,6 +474,11 @@ int launch_apply_t(const bilu_pattern* p, int32_t b, const TV* f, const double* 
 
 }  // namespace
 
+const float* apply_f32_result(const void* work, int32_t n, int32_t b) {
+  // the vector region after the header: y (n*b floats), then the upper sweep's x
+  return reinterpret_cast<const float*>(reinterpret_cast<const char*>(work) + kHeaderBytes) + (size_t)n * b;
+}
+
 void free_schedule(bilu_chunk_schedule* s) {
   if (s->d_mem) cudaFree(s->d_mem);
   s->d_mem = nullptr;

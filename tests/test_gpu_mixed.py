@@ -32,9 +32,10 @@ def B(libbilu):
     return B
 
 
-@pytest.mark.parametrize("b", [1, 2, 3, 5, 8])
-def test_spmv_f32(B, b):
-    S = reservoir_system(11, 7, 5, b, stencil=27, seed=b)
+@pytest.mark.parametrize("b", [1, 2, 3, 4, 5, 6, 7, 8])
+@pytest.mark.parametrize("stencil", [7, 27])
+def test_spmv_f32(B, b, stencil):
+    S = reservoir_system(11, 7, 5, b, stencil=stencil, seed=b)
     rp, ci, vals, _ = device_system(S, DEV)
     vals32 = B.bilu_convert_f32(vals)
     x = np.linspace(-1.0, 1.0, S.n * b)
@@ -43,7 +44,7 @@ def test_spmv_f32(B, b):
     x32 = x.astype(np.float32).astype(np.float64)
     yo = oracle.spmv(S.n, b, S.row_ptr, S.col_idx, v32, x32)
     absy = oracle.spmv(S.n, b, S.row_ptr, S.col_idx, np.abs(v32), np.abs(x32))
-    terms = 27 * b
+    terms = stencil * b
     assert np.all(np.abs(y - yo) <= 2 * gamma(terms) * absy + 1e-300)
 
 
