@@ -197,24 +197,26 @@ __device__ __forceinline__ bool wait_local_flag(const int* flag, int want, Waite
 }
 
 // double -> float, rounded to nearest even, on the integer pipes: rebias the
-// exponent, keep 23 mantissa bits and round on the 29 dropped ones (a carry
-// into the exponent is the correct rounding, up to infinity).  Zero keeps its
-// sign; NaN, infinity and other results outside the normal float range
-// (subnormal, overflow) take the hardware conversion.  The hardware double ->
-// float conversion runs at the FP64 rate on this part; kernels that convert
-// once per FMA use this one.  (On the triangular solves' chain of dependent
-// rows its longer latency loses to the hardware conversion: measured 5-30 %
-// slower there.)
+// exponent, keep 23 mantissa bits and round on the 29 dropped ones (round up
+// when the dropped bits plus the kept last bit exceed half; a carry into the
+// exponent is the correct rounding, up to infinity).  Zero keeps its sign.
+// NaN, infinity and results outside the normal float range (subnormal,
+// overflow) take the hardware conversion.  The two 32-bit halves are taken
+// by an opaque move, so the compiler cannot turn the tests on them back into
+// FP64 comparisons: the FP64 pipe (which also runs the hardware double ->
+// float conversion) is the scarce unit on this part, and kernels that convert
+// once per FMA use this function.  (On the triangular solves' chain of
+// dependent rows its longer latency loses to the hardware conversion:
+// measured 5-30 % slower there.)
 __device__ __forceinline__ float d2f_rn(double d) {
-  const unsigned long long u = (unsigned long long)__double_as_longlong(d);
-  const unsigned e = (unsigned)(u >> 52) & 0x7FFu;
-  const unsigned sign = (unsigned)(u >> 32) & 0x80000000u;
-  if ((u << 1) == 0ull) return __uint_as_float(sign);
-  if (e <= 896u || e >= 1151u) return (float)d;
-  const unsigned mant = (unsigned)(u >> 29) & 0x7FFFFFu;
-  const unsigned rem = (unsigned)u & 0x1FFFFFFFu;
-  unsigned r = ((e - 896u) << 23) | mant;
-  r += (rem > 0x10000000u || (rem == 0x10000000u && (mant & 1u))) ? 1u : 0u;
+  unsigned lo, hi;
+  asm("mov.b64 {%0, %1}, %2;" : "=r"(lo), "=r"(hi) : "d"(d));
+  const unsigned e = (hi >> 20) & 0x7FFu;
+  const unsigned sign = hi & 0x80000000u;
+  if (((hi << 1) | lo) == 0u) return __uint_as_float(sign);
+  if (e - 897u > 253u) return (float)d;  // float exponent outside [1, 254]
+  unsigned r = ((e - 896u) << 23) | ((hi & 0xFFFFFu) << 3) | (lo >> 29);
+  r += (lo & 0x1FFFFFFFu) + (r & 1u) > 0x10000000u ? 1u : 0u;
   return __uint_as_float(sign | r);
 }
 

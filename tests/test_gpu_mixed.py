@@ -49,10 +49,21 @@ def test_spmv_f32(B, b, stencil):
 
 
 def test_convert_f32_rounds_to_nearest(B):
-    x = np.array([1.0, 1.0 + 2.0 ** -30, np.pi, -1e-40, 3.4e38, 1e300, np.nan], np.float64)
+    """FP64 -> FP32 rounding to nearest even (IEEE 754, numpy's cast) on the
+    integer path: exact ties both ways, the carry into the exponent, the
+    overflow boundary, the smallest normal, subnormals, signed zeros, and
+    random values over the whole float range."""
+    edge = [1.0, 1.0 + 2.0 ** -30, np.pi, -1e-40, 3.4e38, 1e300, 0.0, -0.0,
+            1 + 2.0 ** -24, 1 + 3 * 2.0 ** -24, 1 + 2.0 ** -24 + 2.0 ** -50, 1 - 2.0 ** -25,
+            3.4028234663852886e38, 3.4028235677973362e38, 3.4028235677973366e38, 2.0 ** 127 * (2 - 2.0 ** -24),
+            2.0 ** -126, 2.0 ** -126 * (1 - 2.0 ** -24), 2.0 ** -126 * (1 - 2.0 ** -25), -1e-45, -np.inf, np.inf]
+    rng = np.random.default_rng(5)
+    rand = rng.standard_normal(100000) * np.exp(rng.uniform(-90, 90, 100000))
+    x = np.concatenate([np.array(edge), rand, [np.nan]])
     got = B.bilu_convert_f32(torch.from_numpy(x).to(DEV)).cpu().numpy()
-    ref = x.astype(np.float32)
-    assert np.array_equal(got[:-1], ref[:-1]) and np.isnan(got[-1])
+    with np.errstate(over="ignore"):
+        ref = x.astype(np.float32)
+    assert np.array_equal(got[:-1].view(np.uint32), ref[:-1].view(np.uint32)) and np.isnan(got[-1])
 
 
 @pytest.mark.parametrize("b,k", [(3, 0), (3, 1), (4, 2), (8, 1)])
