@@ -583,7 +583,9 @@ def sweep(B, dev, stream, which, tol=1e-8, reps=20, with_oracle=False):
     pool = refs = None
     if with_oracle and which == "c2":
         import multiprocessing as mp
-        pool = mp.get_context("spawn").Pool(min(len(cases), os.cpu_count() or 1))
+        # half the host cores: the solves' host loop (a state read every few
+        # iterations) must not wait for a core
+        pool = mp.get_context("spawn").Pool(min(len(cases), max(1, (os.cpu_count() or 2) // 2)))
         refs = pool.map_async(_oracle_ref_job, cases)
 
     def timed(fn, n):

@@ -53,6 +53,12 @@ int32_t bilu_auto_factor_chunk(const bilu_pattern* p);
  * operands ahead of its dependencies.  Applies to the next launch. */
 int bilu_set_trisolve_warps(int32_t warps);
 
+/* Resident CTAs per SM of the triangular solves' persistent grid: 0 (the
+ * default) for as many as fit, else 1..32 (capped at what fits).  Fewer CTAs
+ * keep fewer chunks in flight and fewer warps polling.  Applies to the next
+ * launch; BILU_ERR_ARG outside 0..32. */
+int bilu_set_trisolve_ctas_per_sm(int32_t ctas);
+
 /* Host copy of the schedule the sync-free solves use for a target of `rows`
  * rows per chunk (the same one bilu_pattern_upload / bilu_pattern_schedule
  * build; the factorization builds one the same way for its own target).  Rows are cut into *nchunks chunks

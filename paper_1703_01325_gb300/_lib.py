@@ -79,6 +79,7 @@ SIGNATURES = {
     "bilu_set_trisolve_chunk": (C.c_int, [C.c_int32]),
     "bilu_get_trisolve_chunk": (C.c_int32, []),
     "bilu_set_trisolve_warps": (C.c_int, [C.c_int32]),
+    "bilu_set_trisolve_ctas_per_sm": (C.c_int, [C.c_int32]),
     "bilu_auto_trisolve_chunk": (C.c_int32, [C.c_void_p]),
     "bilu_auto_factor_chunk": (C.c_int32, [C.c_void_p]),
     "bilu_set_factor_chunk": (C.c_int, [C.c_int32]),

@@ -432,6 +432,10 @@ def bilu_set_trisolve_warps(warps: int):
     _check(L.load().bilu_set_trisolve_warps(warps), "bilu_set_trisolve_warps")
 
 
+def bilu_set_trisolve_ctas_per_sm(ctas: int):
+    _check(L.load().bilu_set_trisolve_ctas_per_sm(ctas), "bilu_set_trisolve_ctas_per_sm")
+
+
 def bilu_get_trisolve_chunk() -> int:
     return int(L.load().bilu_get_trisolve_chunk())
 

@@ -500,6 +500,12 @@ extern "C" int bilu_set_trisolve_warps(int32_t warps) {
   return BILU_OK;
 }
 
+extern "C" int bilu_set_trisolve_ctas_per_sm(int32_t ctas) {
+  if (ctas < 0 || ctas > 32) return BILU_ERR_ARG;
+  trisolve_config().ctas_per_sm = ctas;
+  return BILU_OK;
+}
+
 extern "C" int bilu_set_spin_limit_ns(int64_t ns) {
   if (ns < 1000) return BILU_ERR_ARG;
   trisolve_config().spin_ns = ns;

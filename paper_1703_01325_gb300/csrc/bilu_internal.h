@@ -107,6 +107,7 @@ constexpr long long kDefaultSpinNs = 2000000000LL;  // 2 s
 struct TrisolveConfig {
   int chunk = 0;           // target rows per CTA of the solves (0: by size)
   int warps = 4;           // warps per CTA of the solves (4, 8 or 16)
+  int ctas_per_sm = 0;     // resident CTAs per SM of the solves (0: as many as fit)
   int factor_chunk = 0;    // target rows per CTA of the factorization (0: by size)
   long long spin_ns = kDefaultSpinNs;
   int skip_row = -1;       // test hook: this row of the lower solve is never published

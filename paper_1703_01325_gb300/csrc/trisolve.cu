@@ -210,7 +210,7 @@ __global__ void __launch_bounds__(256) widen_kernel(const float* __restrict__ sr
 // GE: the groups a row's blocks are spread over (a power of two, at most
 // groups_for(B)); the partial sums take log2(GE) reduction steps.  RT: the
 // type of the right-hand side (double r for L, TV z for U').
-template <int B, bool UPPER, typename TV, int kTriWarps, int GE, typename RT>
+template <int B, bool UPPER, typename TV, int kTriWarps, int GE, typename RT, bool DEEP>
 __global__ void __launch_bounds__(kTriWarps * 32) tri_solve_kernel(
     int32_t n, int32_t chunk, int32_t nchunks, const int32_t* __restrict__ bnd, const int32_t* __restrict__ rp,
     const int32_t* __restrict__ ci, const TV* __restrict__ vals,
@@ -253,13 +253,24 @@ __global__ void __launch_bounds__(kTriWarps * 32) tri_solve_kernel(
     }
     for (int q = tid; q < len * B; q += blockDim.x) reinterpret_cast<typename VB::U*>(yl)[q] = VB::kPend;
     __syncthreads();
+    // The next rows of this warp are prefetched: DEEP two rows ahead (nx1
+    // with its remote dependency read, nx2 its row data), else one row ahead,
+    // its dependency read once the current row is published (fewer
+    // registers: at b = 3 in FP64, 64 per thread and eight CTAs per SM
+    // instead of five).
+    constexpr bool kDeep = DEEP;
     RowPre<B, TV, RT> cur, nx1, nx2;
     fetch_row<B, TV, RT>(cur, warp, len, s_i, s_beg, s_end, ci, vals, rhs, g, rr, act, lane);
     fetch_deps<B, TV, RT>(cur, out, lo, hi);
-    fetch_row<B, TV, RT>(nx1, warp + kTriWarps, len, s_i, s_beg, s_end, ci, vals, rhs, g, rr, act, lane);
+    if constexpr (kDeep)
+      fetch_row<B, TV, RT>(nx1, warp + kTriWarps, len, s_i, s_beg, s_end, ci, vals, rhs, g, rr, act, lane);
     for (int pos = warp; pos < len && !dead; pos += kTriWarps) {
-      fetch_row<B, TV, RT>(nx2, pos + 2 * kTriWarps, len, s_i, s_beg, s_end, ci, vals, rhs, g, rr, act, lane);
-      fetch_deps<B, TV, RT>(nx1, out, lo, hi);
+      if constexpr (kDeep) {
+        fetch_row<B, TV, RT>(nx2, pos + 2 * kTriWarps, len, s_i, s_beg, s_end, ci, vals, rhs, g, rr, act, lane);
+        fetch_deps<B, TV, RT>(nx1, out, lo, hi);
+      } else {
+        fetch_row<B, TV, RT>(nx1, pos + kTriWarps, len, s_i, s_beg, s_end, ci, vals, rhs, g, rr, act, lane);
+      }
       const int i = cur.i;
       bool ok = true;
       // The row's own term (r_i or z_i) seeds the sum of group 0 (lanes < B);
@@ -320,8 +331,9 @@ __global__ void __launch_bounds__(kTriWarps * 32) tri_solve_kernel(
         reinterpret_cast<volatile typename VB::U*>(yl)[(size_t)(i - lo) * B + lane] = u;
         if (i != skip_row) publish_value<TV>(out + (size_t)i * B + lane, vt);
       }
+      if constexpr (!kDeep) fetch_deps<B, TV, RT>(nx1, out, lo, hi);
       cur = nx1;
-      nx1 = nx2;
+      if constexpr (kDeep) nx1 = nx2;
     }
   }
 }
@@ -345,20 +357,22 @@ size_t tri_smem_bytes(int chunk, int b) {
 // Persistent grid: as many CTAs as fit on the device at once (cached per
 // shared-memory size; the occupancy query is host work worth skipping per
 // launch).
-template <int B, bool UPPER, typename TV, int kTriWarps, int GE, typename RT>
+template <int B, bool UPPER, typename TV, int kTriWarps, int GE, typename RT, bool DEEP>
 int tri_grid(size_t smem, int nchunks) {
   static size_t last_smem = 0;
   static int last_per_sm = 1;
   if (smem != last_smem) {
-    cudaFuncSetAttribute(tri_solve_kernel<B, UPPER, TV, kTriWarps, GE, RT>,
+    cudaFuncSetAttribute(tri_solve_kernel<B, UPPER, TV, kTriWarps, GE, RT, DEEP>,
                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)std::max<size_t>(smem, 48 * 1024));
     int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tri_solve_kernel<B, UPPER, TV, kTriWarps, GE, RT>,
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tri_solve_kernel<B, UPPER, TV, kTriWarps, GE, RT, DEEP>,
                                                   kTriWarps * 32, smem);
     last_per_sm = per_sm < 1 ? 1 : per_sm;
     last_smem = smem;
   }
-  return std::max(1, std::min(nchunks, last_per_sm * sm_count()));
+  const int cap = trisolve_config().ctas_per_sm;
+  const int per_sm = cap > 0 ? std::min(cap, last_per_sm) : last_per_sm;
+  return std::max(1, std::min(nchunks, per_sm * sm_count()));
 }
 
 // One triangular sweep (the arguments of tri_solve_kernel).
@@ -376,12 +390,27 @@ struct TriArgs {
   int32_t* stop;
 };
 
-template <int B, bool UPPER, typename TV, int W, int GE, typename RT>
-void launch_tri(const TriArgs<TV, RT>& a, size_t smem, cudaStream_t s) {
-  const int grid = tri_grid<B, UPPER, TV, W, GE, RT>(smem, a.nchunks);
-  tri_solve_kernel<B, UPPER, TV, W, GE, RT><<<grid, W * 32, smem, s>>>(
+template <int B, bool UPPER, typename TV, int W, int GE, typename RT, bool DEEP>
+void launch_tri_k(const TriArgs<TV, RT>& a, size_t smem, cudaStream_t s) {
+  const int grid = tri_grid<B, UPPER, TV, W, GE, RT, DEEP>(smem, a.nchunks);
+  tri_solve_kernel<B, UPPER, TV, W, GE, RT, DEEP><<<grid, W * 32, smem, s>>>(
       a.n, a.chunk, a.nchunks, a.bnd, a.rp, a.ci, a.vals, a.ord, a.tick, a.rhs, a.out, a.header, a.spin_ns,
       a.skip_row, a.stop);
+}
+
+// Prefetch depth, measured on 128x128x64 and 96x96x48 seven-point grids and
+// the 160x160x80 27-point ILU(2) grid: one row ahead is faster in FP64 for
+// b >= 3 (b = 3, 4, 8 by 5-17 %: fewer registers, more CTAs per SM) unless
+// the widest row takes more than four passes over the groups (27-point
+// ILU(2): 29 % slower); two rows ahead wins in FP32 (3 %) and at b <= 2.
+template <int B, bool UPPER, typename TV, int W, int GE, typename RT>
+void launch_tri(const TriArgs<TV, RT>& a, int32_t max_blocks, size_t smem, cudaStream_t s) {
+  if constexpr (sizeof(TV) == 4 || B <= 2) {
+    launch_tri_k<B, UPPER, TV, W, GE, RT, true>(a, smem, s);
+  } else {
+    if ((max_blocks + GE - 1) / GE > 4) launch_tri_k<B, UPPER, TV, W, GE, RT, true>(a, smem, s);
+    else launch_tri_k<B, UPPER, TV, W, GE, RT, false>(a, smem, s);
+  }
 }
 
 // The fewest groups (a power of two, at least groups_for(B) / 4) that hold
@@ -393,10 +422,10 @@ void launch_tri_groups(const TriArgs<TV, RT>& a, int32_t max_blocks, size_t smem
   constexpr int G = groups_for(B);
   const int32_t need = max_blocks;
   if constexpr (W == 4) {
-    if (need <= G / 4) return launch_tri<B, UPPER, TV, W, G / 4, RT>(a, smem, s);
-    if (need <= G / 2) return launch_tri<B, UPPER, TV, W, G / 2, RT>(a, smem, s);
+    if (need <= G / 4) return launch_tri<B, UPPER, TV, W, G / 4, RT>(a, need, smem, s);
+    if (need <= G / 2) return launch_tri<B, UPPER, TV, W, G / 2, RT>(a, need, smem, s);
   }
-  launch_tri<B, UPPER, TV, W, G, RT>(a, smem, s);
+  launch_tri<B, UPPER, TV, W, G, RT>(a, need, smem, s);
 }
 
 // L y = r (y in TV), z = D^{-1} y in place, U' x = z (x in TV: the caller's

@@ -442,3 +442,28 @@ def test_compute_calls_need_an_uploaded_pattern(B):
     with pytest.raises(B.BiluError) as e:
         B.bilu_factor(P, 3, vals)
     assert e.value.status == L.BILU_ERR_STATE
+
+
+@pytest.mark.parametrize("b", [2, 3, 8])
+def test_apply_is_independent_of_residency(B, b):
+    """The solves' result does not depend on how many CTAs share the chunks
+    (each row's sum runs in a fixed order): FP64 and FP32 applies with one
+    resident CTA per SM equal the default grid's bit for bit, and the oracle's
+    x.  b = 2 prefetches two rows ahead, b = 3 and 8 one row ahead in FP64."""
+    S = reservoir_system(20, 14, 9, b, seed=30 + b)
+    o = OracleRun(S.n, b, S.row_ptr, S.col_idx, S.vals, 1)
+    _, _, vals, rhs = device_system(S, DEV)
+    P = B.bilu_symbolic(S.n, S.row_ptr, S.col_idx, 1).upload()
+    F, _ = B.bilu_factor(P, b, vals)
+    F32 = B.bilu_convert_f32(F)
+    x64 = B.bilu_apply(P, b, F, rhs).cpu().numpy()
+    x32 = B.bilu_apply_f32(P, b, F32, rhs).cpu().numpy()
+    try:
+        B.bilu_set_trisolve_ctas_per_sm(1)
+        y64 = B.bilu_apply(P, b, F, rhs).cpu().numpy()
+        y32 = B.bilu_apply_f32(P, b, F32, rhs).cpu().numpy()
+    finally:
+        B.bilu_set_trisolve_ctas_per_sm(0)
+    assert np.array_equal(x64.view(np.int64), y64.view(np.int64))
+    assert np.array_equal(x32.view(np.int64), y32.view(np.int64))
+    assert rel_maxerr(x64, o.apply(S.rhs)) <= TOL_APPLY
