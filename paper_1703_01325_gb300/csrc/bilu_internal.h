@@ -140,10 +140,15 @@ class ProfScope {
 // ---- kernels (launchers return cudaError_t as int) ----
 int launch_spmv(int32_t n, int32_t b, const int32_t* rp, const int32_t* ci, const double* vals,
                 const double* x, double* y, void* stream, const int32_t* stop = nullptr);
+// FP32 SpMV; allow_staged = false keeps to the direct kernel (rows too long
+// for the staged kernel's buffers: spmv_f32_staging_fits).
 int launch_spmv_f32(int32_t n, int32_t b, const int32_t* rp, const int32_t* ci, const float* vals,
-                    const double* x, double* y, void* stream, const int32_t* stop = nullptr);
+                    const double* x, double* y, void* stream, const int32_t* stop = nullptr,
+                    bool allow_staged = true);
 int launch_spmv_f32x(int32_t n, int32_t b, const int32_t* rp, const int32_t* ci, const float* vals,
-                     const float* x, double* y, void* stream, const int32_t* stop = nullptr);
+                     const float* x, double* y, void* stream, const int32_t* stop = nullptr,
+                     bool allow_staged = true);
+bool spmv_f32_staging_fits(int32_t n, long long nnzb);
 // The FP32 apply's result in FP32 (the vector the FP32 apply widens into its
 // FP64 output), inside its workspace.
 const float* apply_f32_result(const void* work, int32_t n, int32_t b);

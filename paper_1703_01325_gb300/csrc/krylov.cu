@@ -478,15 +478,23 @@ int run_bicgstab_mixed(const bilu_pattern* p, const bilu_bsr* A, const float* va
   double* d = reinterpret_cast<double*>(tail + vec);
   double* norms = reinterpret_cast<double*>(tail + 2 * vec);  // [(r, r), (rhs, rhs)]
   double* partials = reinterpret_cast<double*>(reinterpret_cast<char*>(work) + align256(sizeof(KState)));
+  // A's block count picks the FP32 SpMV kernel (rows of at most about seven
+  // blocks are staged in shared memory)
+  // (a failed read leaves nnzb = 0, and the solve's own CUDA checks report it)
+  int32_t nnzb = 0;
+  if (cudaMemcpyAsync(&nnzb, A->row_ptr + n, sizeof(int32_t), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    nnzb = 0;
+  const bool staged = spmv_f32_staging_fits(n, nnzb);
   KOps ops;
   ops.spmv = [=](const double* xin, double* yout, int32_t* stop, void*) {
-    return launch_spmv_f32(n, b, A->row_ptr, A->col_idx, vals32, xin, yout, stream, stop);
+    return launch_spmv_f32(n, b, A->row_ptr, A->col_idx, vals32, xin, yout, stream, stop, staged);
   };
   // p_hat and s_hat come from the FP32 apply: its FP32 result is x rounded to
   // FP32 exactly, so the SpMV reads that (the same products and sums)
   ops.spmv_applied = [=](const double*, double* yout, int32_t* stop, void* aw) {
     return launch_spmv_f32x(n, b, A->row_ptr, A->col_idx, vals32, apply_f32_result(aw, n, b), yout, stream,
-                            stop);
+                            stop, staged);
   };
   ops.apply = [=](const double* rin, double* zout, int32_t* stop, void* aw) {
     return launch_apply_f32(p, b, f32, rin, zout, aw, stop, stream);

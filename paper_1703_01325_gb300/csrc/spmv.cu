@@ -269,12 +269,13 @@ int launch_spmv_f32_staged(int32_t n, const int32_t* rp, const int32_t* ci, cons
 }
 
 // FP32 values, x of type XT: the staged kernel for b <= 5 with 16-byte aligned
-// column indices and values, else the direct kernel.
+// column indices and values (unless the caller knows the rows are too long
+// for its buffers), else the direct kernel.
 template <typename XT>
 int launch_spmv_f32_any(int32_t n, int32_t b, const int32_t* rp, const int32_t* ci, const float* vals,
-                        const XT* x, double* y, void* stream, const int32_t* stop) {
+                        const XT* x, double* y, void* stream, const int32_t* stop, bool allow_staged) {
   if (n == 0) return 0;
-  if (b <= 5 && ((((uintptr_t)ci) | ((uintptr_t)vals)) & 15u) == 0) {
+  if (allow_staged && b <= 5 && ((((uintptr_t)ci) | ((uintptr_t)vals)) & 15u) == 0) {
     switch (b) {
       case 1: return launch_spmv_f32_staged<1, XT>(n, rp, ci, vals, x, y, stream, stop);
       case 2: return launch_spmv_f32_staged<2, XT>(n, rp, ci, vals, x, y, stream, stop);
@@ -294,13 +295,20 @@ int launch_spmv(int32_t n, int32_t b, const int32_t* rp, const int32_t* ci, cons
 }
 
 int launch_spmv_f32(int32_t n, int32_t b, const int32_t* rp, const int32_t* ci, const float* vals,
-                    const double* x, double* y, void* stream, const int32_t* stop) {
-  return launch_spmv_f32_any<double>(n, b, rp, ci, vals, x, y, stream, stop);
+                    const double* x, double* y, void* stream, const int32_t* stop, bool allow_staged) {
+  return launch_spmv_f32_any<double>(n, b, rp, ci, vals, x, y, stream, stop, allow_staged);
 }
 
 int launch_spmv_f32x(int32_t n, int32_t b, const int32_t* rp, const int32_t* ci, const float* vals,
-                     const float* x, double* y, void* stream, const int32_t* stop) {
-  return launch_spmv_f32_any<float>(n, b, rp, ci, vals, x, y, stream, stop);
+                     const float* x, double* y, void* stream, const int32_t* stop, bool allow_staged) {
+  return launch_spmv_f32_any<float>(n, b, rp, ci, vals, x, y, stream, stop, allow_staged);
+}
+
+bool spmv_f32_staging_fits(int32_t n, long long nnzb) {
+  // a stage buffer holds R rows of 7 blocks plus alignment slack: on average
+  // at most 7.2 blocks per row (36 / 5), else most groups would read global
+  // memory from a kernel whose shared memory still costs L1
+  return nnzb * 5 <= (long long)n * 36;
 }
 
 int launch_convert_f32(const double* src, float* dst, long long count, void* stream, const int32_t* stop) {
