@@ -162,6 +162,19 @@ __device__ __forceinline__ void fetch_row(RowPre<B, TV, RT>& p, int pos, int len
   if (lane < B) p.own = rhs[(size_t)p.i * B + lane];
 }
 
+// The row two turns ahead, for the one-row prefetch: its first block's column
+// index and values are pulled into L2 without holding registers.
+template <int B, typename TV>
+__device__ __forceinline__ void prefetch_row_l2(int pos, int len, const int* s_beg, const int* s_end,
+                                                const int32_t* __restrict__ ci, const TV* __restrict__ vals,
+                                                int g, int rr, bool act) {
+  if (pos >= len || !act) return;
+  const int t = s_beg[pos] + g;
+  if (t >= s_end[pos]) return;
+  asm volatile("prefetch.global.L2 [%0];" ::"l"(ci + t));
+  asm volatile("prefetch.global.L2 [%0];" ::"l"(vals + (size_t)t * (B * B) + rr));
+}
+
 // Stage B: a dependency outside the chunk is usually final already: read it
 // now (relaxed); if it still holds the pending pattern it is waited for later.
 template <int B, typename TV, typename RT>
@@ -270,6 +283,7 @@ __global__ void __launch_bounds__(kTriWarps * 32) tri_solve_kernel(
         fetch_deps<B, TV, RT>(nx1, out, lo, hi);
       } else {
         fetch_row<B, TV, RT>(nx1, pos + kTriWarps, len, s_i, s_beg, s_end, ci, vals, rhs, g, rr, act, lane);
+        prefetch_row_l2<B, TV>(pos + 2 * kTriWarps, len, s_beg, s_end, ci, vals, g, rr, act);
       }
       const int i = cur.i;
       bool ok = true;
