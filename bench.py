@@ -50,8 +50,8 @@ FP64_PEAK_TFLOPS = 1.196  # measured FP64 FMA rate of this GB300 (FMA = 2 flops)
 # the algorithmic bytes.  Missing entries (no capture of the kernel as it
 # stands) report null.
 NCU_TRAFFIC = {
-    ("grid128x128x64_7pt_b3", 1, "upper_solve"): 552482525,   # 1.052 x algorithmic
-    ("grid128x128x64_7pt_b3", 1, "lower_solve"): 552274623,   # 1.052 x
+    ("grid128x128x64_7pt_b3", 1, "upper_solve"): 552320350,   # 1.052 x algorithmic
+    ("grid128x128x64_7pt_b3", 1, "lower_solve"): 551958807,   # 1.051 x
     ("grid128x128x64_7pt_b3", 1, "diag_scale"): 100673612,    # 0.800 x (z stays in L2)
     ("grid128x128x64_7pt_b3", 1, "spmv"): 601747660,          # 0.991 x
 }
