@@ -266,11 +266,11 @@ __global__ void __launch_bounds__(kTriWarps * 32) tri_solve_kernel(
     }
     for (int q = tid; q < len * B; q += blockDim.x) reinterpret_cast<typename VB::U*>(yl)[q] = VB::kPend;
     __syncthreads();
-    // The next rows of this warp are prefetched: DEEP two rows ahead (nx1
-    // with its remote dependency read, nx2 its row data), else one row ahead,
-    // its dependency read once the current row is published (fewer
-    // registers: at b = 3 in FP64, 64 per thread and eight CTAs per SM
-    // instead of five).
+    // The next rows of this warp are prefetched: DEEP two rows ahead in
+    // registers (nx1 with its remote dependency read, nx2 its row data), else
+    // one row ahead, its dependency read once the current row is published,
+    // and the row after it pulled into L2 (fewer registers: at b = 3 in FP64,
+    // 70 per thread and seven CTAs per SM instead of 90 and five).
     constexpr bool kDeep = DEEP;
     RowPre<B, TV, RT> cur, nx1, nx2;
     fetch_row<B, TV, RT>(cur, warp, len, s_i, s_beg, s_end, ci, vals, rhs, g, rr, act, lane);
@@ -413,13 +413,15 @@ void launch_tri_k(const TriArgs<TV, RT>& a, size_t smem, cudaStream_t s) {
 }
 
 // Prefetch depth, measured on 128x128x64 and 96x96x48 seven-point grids and
-// the 160x160x80 27-point ILU(2) grid: one row ahead is faster in FP64 for
-// b >= 3 (b = 3, 4, 8 by 5-17 %: fewer registers, more CTAs per SM) unless
-// the widest row takes more than four passes over the groups (27-point
-// ILU(2): 29 % slower); two rows ahead wins in FP32 (3 %) and at b <= 2.
+// the 160x160x80 27-point ILU(2) grid: one row in registers and the row
+// after it in L2 is faster than two rows in registers (fewer registers, more
+// CTAs per SM: FP64 b = 3 1380 -> 1255 us, FP32 b = 3 972 -> 926 us, b = 4
+// 4-21 %, FP64 b = 2 k = 0 6 %) unless the widest row takes more than four
+// passes over the groups (27-point ILU(2): 29 % slower) or the FP32 blocks are
+// 6 x 6 or larger (FP32 b = 8: 6 % slower).
 template <int B, bool UPPER, typename TV, int W, int GE, typename RT>
 void launch_tri(const TriArgs<TV, RT>& a, int32_t max_blocks, size_t smem, cudaStream_t s) {
-  if constexpr (sizeof(TV) == 4 || B <= 2) {
+  if constexpr (sizeof(TV) == 4 && B >= 6) {
     launch_tri_k<B, UPPER, TV, W, GE, RT, true>(a, smem, s);
   } else {
     if ((max_blocks + GE - 1) / GE > 4) launch_tri_k<B, UPPER, TV, W, GE, RT, true>(a, smem, s);
