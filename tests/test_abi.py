@@ -63,3 +63,28 @@ def test_compute_calls_never_build_a_schedule(libbilu):
         assert P.schedule_info() == {"solve_rows": 0, "factor_rows": 0}
     finally:
         B.bilu_set_trisolve_chunk(old)
+
+
+def test_tuning_setters_and_spmv_reject_bad_arguments(libbilu):
+    """Argument checks that run before any CUDA call: the solves' knobs take
+    only their documented ranges, and the FP32 SpMV calls reject a bad block
+    size, missing pointers and x aliasing y."""
+    import ctypes as C
+
+    from paper_1703_01325_gb300 import _lib as L
+    lib = L.load()
+    for bad in (-1, 33):
+        assert lib.bilu_set_trisolve_ctas_per_sm(bad) == L.BILU_ERR_ARG
+    for good in (0, 1, 32, 0):
+        assert lib.bilu_set_trisolve_ctas_per_sm(good) == L.BILU_OK
+    for bad in (2, 5, 32):
+        assert lib.bilu_set_trisolve_warps(bad) == L.BILU_ERR_ARG
+    assert lib.bilu_set_trisolve_warps(4) == L.BILU_OK
+    p = C.c_void_p(0x1000)  # never dereferenced: the checks come first
+    for fn in (lib.bsr_spmv_f32, lib.bsr_spmv_f32x):
+        assert fn(10, 0, p, p, p, p, C.c_void_p(0x2000), None) == L.BILU_ERR_ARG
+        assert fn(10, 9, p, p, p, p, C.c_void_p(0x2000), None) == L.BILU_ERR_ARG
+        assert fn(-1, 3, p, p, p, p, C.c_void_p(0x2000), None) == L.BILU_ERR_ARG
+        assert fn(10, 3, None, p, p, p, C.c_void_p(0x2000), None) == L.BILU_ERR_ARG
+        assert fn(10, 3, p, p, p, C.c_void_p(0x3000), C.c_void_p(0x3000), None) == L.BILU_ERR_ARG
+        assert fn(0, 3, p, p, p, p, C.c_void_p(0x2000), None) == L.BILU_OK  # nothing to do
