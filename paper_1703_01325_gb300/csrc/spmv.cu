@@ -9,10 +9,13 @@
 // every byte of the warp's contiguous value range is used.  Values are
 // streamed with cache-streaming loads; x stays in L2 for the gathers.
 // In FP64 the kernel is bound by the FP64 pipe; in FP32 it is bound by load
-// latency, so the FP32 kernel issues the loads of four blocks (column
+// latency, so the FP32 kernels issue the loads of four blocks (column
 // indices, then values and x) before their FMAs, which run in the same order
-// as one block at a time (identical sums).  The FP32 kernel takes x in FP64
-// and rounds it to nearest on the integer pipes, one component per lane.
+// as one block at a time (identical sums).  For b <= 5 the FP32 path first
+// stages each warp's whole value range in shared memory (one batch of
+// 16-byte asynchronous copies, spmv_f32_staged_kernel below).  x is either
+// FP64, rounded to nearest on the integer pipes one component per lane, or
+// FP32 already (the FP32 preconditioner's own result).
 #include <cuda_runtime.h>
 
 #include <algorithm>
