@@ -416,17 +416,15 @@ void launch_tri_k(const TriArgs<TV, RT>& a, size_t smem, cudaStream_t s) {
 // the 160x160x80 27-point ILU(2) grid: one row in registers and the row
 // after it in L2 is faster than two rows in registers (fewer registers, more
 // CTAs per SM: FP64 b = 3 1380 -> 1255 us, FP32 b = 3 972 -> 926 us, b = 4
-// 4-21 %, FP64 b = 2 k = 0 6 %) unless the widest row takes more than four
-// passes over the groups (27-point ILU(2): 29 % slower) or the FP32 blocks are
-// 6 x 6 or larger (FP32 b = 8: 6 % slower).
+// 4-21 %, FP32 b = 6 k = 0 8 %, FP64 b = 2 k = 0 6 %) while the widest row
+// fits in one pass over the groups (FP32) or four (FP64).  Wider rows keep
+// two rows in registers: FP32 b = 6 with 2-4 passes is 20-29 % slower, FP32
+// b = 8 with 2 passes 6 %, FP64 27-point ILU(2) with 7 passes 29 %.
 template <int B, bool UPPER, typename TV, int W, int GE, typename RT>
 void launch_tri(const TriArgs<TV, RT>& a, int32_t max_blocks, size_t smem, cudaStream_t s) {
-  if constexpr (sizeof(TV) == 4 && B >= 6) {
-    launch_tri_k<B, UPPER, TV, W, GE, RT, true>(a, smem, s);
-  } else {
-    if ((max_blocks + GE - 1) / GE > 4) launch_tri_k<B, UPPER, TV, W, GE, RT, true>(a, smem, s);
-    else launch_tri_k<B, UPPER, TV, W, GE, RT, false>(a, smem, s);
-  }
+  const int passes = (max_blocks + GE - 1) / GE;
+  if (passes > (sizeof(TV) == 4 ? 1 : 4)) launch_tri_k<B, UPPER, TV, W, GE, RT, true>(a, smem, s);
+  else launch_tri_k<B, UPPER, TV, W, GE, RT, false>(a, smem, s);
 }
 
 // The fewest groups (a power of two, at least groups_for(B) / 4) that hold
