@@ -72,6 +72,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-precision", action="store_true", help="skip the FP32-preconditioner comparison")
+    ap.add_argument("--no-c2", action="store_true", help="skip the brief b x k sweep of the 96 x 96 x 48 grid")
     ap.add_argument("--sweep", choices=["c2", "c3"], default=None,
                     help="instead of the bench line: one JSON line per configuration of the 96 x 96 x 48 "
                          "b x k sweep (c2) or of the 160 x 160 x 80 27-point ILU(2) case (c3)")
@@ -552,7 +553,7 @@ def _oracle_ref_job(job):
     return job, ref
 
 
-def sweep(B, dev, stream, which, tol=1e-8, reps=20, with_oracle=False):
+def sweep(B, dev, stream, which, tol=1e-8, reps=20, with_oracle=False, solve_reps=None, emit=True):
     """Per-configuration numbers, one JSON line each: the device set-up
     (symbolic phase and schedules, bilu_symbolic_gpu + bilu_pattern_upload),
     FP64 and FP32 factorization, FP64 and FP32 apply and SpMV (mean CUDA-event
@@ -575,10 +576,11 @@ def sweep(B, dev, stream, which, tol=1e-8, reps=20, with_oracle=False):
     from paper_1703_01325_gb300.reservoir import WORKLOADS, reservoir_system
     if which == "c2":
         cases = [("grid96x96x48_7pt", b, k) for b in (2, 4, 6, 8) for k in (0, 1, 2)]
-        maxit, solve_reps = 5000, 3
+        maxit, nrep = 5000, 3
     else:
         cases = [("grid160x160x80_27pt_b3", 3, 2)]
-        maxit, solve_reps = 300, 1
+        maxit, nrep = 300, 1
+    solve_reps = solve_reps or nrep
     hbm, _ = peaks()
     pool = refs = None
     if with_oracle and which == "c2":
@@ -609,11 +611,14 @@ def sweep(B, dev, stream, which, tol=1e-8, reps=20, with_oracle=False):
         return {"ms": round(e0.elapsed_time(e1), 2), "iters": si.iters, "true_relres": si.true_relres,
                 "status": si.status}
 
-    rows, xs = [], {}
+    rows, xs, systems = [], {}, {}
     for wl, b, k in cases:
-        cfg = dict(WORKLOADS[wl])
-        cfg["b"] = b
-        S = reservoir_system(**cfg)
+        if (wl, b) not in systems:  # the matrix does not depend on k
+            systems.clear()
+            cfg = dict(WORKLOADS[wl])
+            cfg["b"] = b
+            systems[(wl, b)] = reservoir_system(**cfg)
+        S = systems[(wl, b)]
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         P = B.bilu_symbolic_gpu(S.n, S.row_ptr, S.col_idx, k)
@@ -671,7 +676,8 @@ def sweep(B, dev, stream, which, tol=1e-8, reps=20, with_oracle=False):
                 # state reads only ever add time
                 runs.sort(key=lambda r: r["ms"])
                 row[tag] = dict(runs[0], runs=len(runs))
-                xs[(b, k, tag)] = x.cpu().numpy()
+                if refs is not None:
+                    xs[(b, k, tag)] = x.cpu().numpy()
             if with_oracle:
                 row["cpu_baseline"] = oracle_kernel_times(S, k)
         else:
@@ -697,7 +703,7 @@ def sweep(B, dev, stream, which, tol=1e-8, reps=20, with_oracle=False):
             H.close()
             del mw, gw
         rows.append(row)
-        if refs is None:
+        if refs is None and emit:
             print(json.dumps(row), flush=True)
         del F, F32, fw, aw, sw, V32, vals
         P.close()
@@ -713,7 +719,27 @@ def sweep(B, dev, stream, which, tol=1e-8, reps=20, with_oracle=False):
                 xv = xs[(row["b"], row["k"], tag)]
                 row[tag]["x_rel_err_vs_oracle"] = float(np.linalg.norm(xv - ref["x"]) / np.linalg.norm(ref["x"]))
             row["oracle_reference"] = {k2: ref[k2] for k2 in ("iters", "true_relres", "status", "seconds")}
-            print(json.dumps(row), flush=True)
+            if emit:
+                print(json.dumps(row), flush=True)
+    return rows
+
+
+def c2_summary(rows):
+    """The b x k sweep of the 96 x 96 x 48 grid in brief: per configuration
+    the FP64 and FP32 apply and SpMV times and one FP64 and one
+    FP32-preconditioned BiCGSTAB solve to 1e-8 (factorization excluded)."""
+    out = []
+    for r in rows:
+        f64, f32 = r["bicgstab_f64"], r["bicgstab_f32prec"]
+        out.append({"b": r["b"], "k": r["k"], "levels": r["levels_lower"],
+                    "apply_us": {"f64": r["apply_f64"]["us"], "f32": r["apply_f32"]["us"]},
+                    "apply_frac_hbm_f64": r["apply_f64"]["frac_hbm"],
+                    "spmv_us": {"f64": r["spmv_f64"]["us"], "f32": r["spmv_f32"]["us"],
+                                "f32_x32": r["spmv_x32_f32"]["us"]},
+                    "bicgstab_f64": {"ms": f64["ms"], "iters": f64["iters"], "status": f64["status"]},
+                    "bicgstab_f32prec": {"ms": f32["ms"], "iters": f32["iters"], "status": f32["status"]},
+                    "f32prec_speedup": round(f64["ms"] / f32["ms"], 3) if f32["ms"] > 0 else None})
+    return out
 
 
 def kernel_case(args):
@@ -882,13 +908,22 @@ def main():
                "h2d_bytes_per_step": int(h_vals.numel() * 8 + h_rhs.numel() * 8),
                "d2h_bytes_per_step": int(h_x.numel() * 8)}
 
-    small = prec = f32 = c2 = None
+    small = prec = f32 = c2 = sweep_c2 = None
     if rank == 0 and args.workload == WORKLOAD and not args.no_extras:
         small = ms_to_tol_small(B, dev, stream)
         c2 = ms_to_tol_c2(B, dev, stream)
         f32 = fp32_kernel_rates(B, S, P, F, vals, rhs, rp, ci, dev, stream)
         if not args.no_precision:
             prec = precision_compare(B, dev, stream, with_oracle=not args.no_cpu)
+        if not args.no_c2:
+            # the b x k sweep in brief (one solve each, no oracle references;
+            # `--sweep c2 --oracle` gives the full record); a failure here
+            # must not cost the bench line
+            try:
+                sweep_c2 = {"workload": "grid96x96x48_7pt", "tol": 1e-8,
+                            "rows": c2_summary(sweep(B, dev, stream, "c2", reps=5, solve_reps=1, emit=False))}
+            except Exception as exc:  # noqa: BLE001
+                sweep_c2 = {"error": f"{type(exc).__name__}: {exc}"}
     if rank != 0:
         if dist:
             dist.destroy_process_group()
@@ -931,7 +966,7 @@ def main():
         "factor_ms": round(factor_ms / args.steps, 3), "symbolic_ms": round(symbolic_ms, 1),
         "per_iteration_ms": round((ms - factor_ms / args.steps) / max(gpu_iters, 1), 4),
         "ms_to_tol_small": small, "ms_to_tol_c2": c2, "fp64_issue": ceil,
-        "fp32_prec_vs_fp64": prec, "fp32_kernels": f32,
+        "fp32_prec_vs_fp64": prec, "fp32_kernels": f32, "sweep_c2": sweep_c2,
         "kernels": kern, "roofline": roof, "e2e": e2e, "cpu_baseline": cpu,
         "gpu_launches": int(launches), "clocks": clk,
         "fp64_alu": {"peak_tflops": FP64_PEAK_TFLOPS,
