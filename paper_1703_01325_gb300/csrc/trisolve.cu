@@ -27,11 +27,13 @@
 //    memory (slots reset to pending when the chunk starts), one outside the
 //    chunk in global memory (one L2 round trip per poll).  No separate flag,
 //    no fence, no acquire on the hot path;
-//  * loads run ahead of the dependency chain in two stages: the column
-//    indices and values (and the row's own operands) of the row a warp will
-//    solve two turns later, and optimistic reads of the next row's
-//    dependencies outside the chunk (which need those column indices), are
-//    issued before the current row's waits start;
+//  * loads run ahead of the dependency chain: the column index and values of
+//    the first block (and the row's own operand) of the row a warp solves
+//    next, an optimistic read of that row's dependency outside the chunk
+//    (which needs the column index) once the current row is published, and
+//    an L2 prefetch of the row after it, which holds no registers; for rows
+//    of several passes over the groups (one in FP32, four in FP64) two rows
+//    are held in registers instead, the dependency read a turn ahead;
 //  * forward progress: a row only waits on rows of earlier positions in its
 //    chunk or of earlier tickets, all held by running warps; every wait is
 //    bounded and gives up with BILU_ERR_TIMEOUT (never a trap), and no warp
